@@ -1,0 +1,243 @@
+/*
+ * gp.h -- C-ABI of the GB300 library for linear-time multilevel graph
+ * partitioning via edge sparsification (Gottesbueren, Maas, Rosch, Sanders,
+ * Seemaier, "Linear-Time Multilevel Graph Partitioning via Edge
+ * Sparsification").
+ *
+ * Problem (Sec. 2): an undirected graph G = (V, E, c, w) with node weights
+ * c > 0 and edge weights w > 0 is split into k blocks of weight at most
+ * L_max = (1 + eps) * ceil(c(V) / k), minimising the cut, the total weight
+ * of edges between blocks.
+ *
+ * Graphs are symmetric CSR arrays in DEVICE memory: every undirected edge is
+ * stored in both rows, rows hold no self-loops and no duplicates.  Ids and
+ * weights are int32; xadj is int32 (at most 2^31 - 1 entries).  All work is
+ * ordered on the context's stream; functions that return a host scalar
+ * synchronise that stream before returning.  No function throws; every
+ * function returns a gp_status, and on error the outputs are undefined and
+ * gp_last_error() describes the failure.  Results are deterministic: a call
+ * with the same inputs, parameters and seed returns the same bits, and equal
+ * those of the CPU oracle of the same method.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GP_OK = 0,
+  GP_ERR_INVALID = 1,    /* malformed graph or argument */
+  GP_ERR_INFEASIBLE = 2, /* a node is heavier than L_max */
+  GP_ERR_OVERFLOW = 3,   /* total node or edge weight exceeds 2^31 - 1 */
+  GP_ERR_OOM = 4,        /* the allocator returned NULL */
+  GP_ERR_CUDA = 5,       /* a CUDA runtime call failed */
+  GP_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
+  GP_ERR_BUDGET = 7      /* a request does not fit the memory budget */
+} gp_status;
+
+/* A graph in device memory.  m2 = number of CSR entries = 2 |E|. */
+typedef struct gp_graph {
+  int32_t n;
+  int64_t m2;
+  int32_t *xadj;   /* n + 1 row offsets */
+  int32_t *adjncy; /* m2 neighbour ids */
+  int32_t *vwgt;   /* n node weights c(v) > 0 */
+  int32_t *adjwgt; /* m2 edge weights w(e) > 0, equal in both directions */
+} gp_graph;
+
+/*
+ * Device-memory allocator.  alloc returns `bytes` of device memory usable in
+ * stream order on `stream` (NULL on failure); free returns memory allocated
+ * by alloc.  When no allocator is given the library uses cudaMallocAsync /
+ * cudaFreeAsync on the context stream.
+ */
+typedef struct gp_allocator {
+  void *(*alloc)(size_t bytes, void *user, void *stream);
+  void (*free)(void *ptr, size_t bytes, void *user, void *stream);
+  void *user;
+} gp_allocator;
+
+/* Sparsifier choice (Sec. 4.2). */
+enum { GP_SPARSIFY_NONE = 0, GP_SPARSIFY_TWEIGHT = 1, GP_SPARSIFY_UNIFORM = 2 };
+
+/*
+ * Method parameters.  gp_config_default() gives the paper's values:
+ * tau_e = tau_d = 1/2 and rho = 4 (Sec. 6.1), U = c(V) / (160 k), at most
+ * 2.5x node reduction per level and a coarsest size of 160 k (Sec. 4.3),
+ * weighted threshold sampling (Sec. 6.2), and this library's fixed LP
+ * schedule (5 rounds of 8 synchronous sub-rounds, 8 bisection trials).
+ */
+typedef struct gp_config {
+  int32_t tau_e_num, tau_e_den;       /* edge bound tau_e */
+  int32_t tau_d_num, tau_d_den;       /* density bound tau_d */
+  int32_t rho_num, rho_den;           /* trigger factor rho */
+  int32_t cluster_factor;             /* U = W / (cluster_factor * k) */
+  int32_t coarsest_factor;            /* coarsen while n > coarsest_factor * k */
+  int32_t shrink_num, shrink_den;     /* at most num/den node reduction per level */
+  int32_t min_shrink_num, min_shrink_den; /* stop when n' * num > n * den */
+  int32_t lp_rounds, lp_subrounds;    /* clustering LP schedule */
+  int32_t ref_rounds;                 /* refinement LP rounds */
+  int32_t ip_trials;                  /* greedy-growing trials per bisection */
+  int32_t sparsifier;                 /* GP_SPARSIFY_* */
+  int32_t two_hop, isolated;          /* enable 2-hop / isolated-node clustering */
+  int32_t max_levels;                 /* cap on the hierarchy depth (<= 64) */
+  int32_t dbg_max_subrounds;          /* < 0: no limit; else stop clustering LP early (tests) */
+  int32_t validate;                   /* gp_partition: 1 = full input validation */
+} gp_config;
+
+/* Per-level record of one coarsening step (Alg. 1 quantities). */
+typedef struct gp_level_stats {
+  int32_t n, n_next;
+  int64_t m, m_coarse, m_hat, m_next;
+  int32_t triggered, omega_t;
+  int64_t n_greater, n_equal;
+  uint64_t threshold;
+  int32_t lp_subrounds;
+  int64_t lp_moves, clusters_lp, clusters_2hop, clusters_final;
+} gp_level_stats;
+
+#define GP_MAX_LEVELS 64
+typedef struct gp_partition_stats {
+  int32_t levels;
+  gp_level_stats lv[GP_MAX_LEVELS];
+  int64_t U, Lmax, W, ip_cut, cut, rebalance_moves;
+  int32_t n_coarsest;
+  double ms_coarsen, ms_initial, ms_uncoarsen, ms_total; /* device time per phase */
+} gp_partition_stats;
+
+typedef struct gp_ctx gp_ctx;
+
+/* Default parameters (see gp_config). */
+void gp_config_default(gp_config *cfg);
+
+/*
+ * Creates a context on CUDA device `device` whose work is ordered on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  `alloc` may
+ * be NULL.  The context keeps no graph between calls.
+ */
+gp_status gp_create(gp_ctx **ctx, int device, void *stream, const gp_allocator *alloc);
+void gp_destroy(gp_ctx *ctx);
+/* Text of the last error on this context ("" if none).  Owned by ctx. */
+const char *gp_last_error(const gp_ctx *ctx);
+/* Library build string (version, compute capability compiled for). */
+const char *gp_version(void);
+
+/*
+ * One coarsening clustering of G_level (Sec. 3, Sec. 4.1): size-constrained
+ * label propagation under the cluster bound U, then 2-hop clustering and
+ * isolated-node clustering, limited to a 2.5x node reduction (Sec. 4.3).
+ * cmap (device, n entries, caller-owned) receives dense coarse ids in
+ * [0, *n_coarse), numbered by the rank of each cluster's id.  `label`
+ * (device, n entries, may be NULL) receives the cluster id of every node.
+ * `stats` (host, may be NULL) receives the step's counters.  Synchronises.
+ */
+gp_status gp_coarsen(gp_ctx *ctx, const gp_graph *g, int64_t U, int32_t level, uint64_t seed,
+                     const gp_config *cfg, int32_t *cmap, int32_t *label, int32_t *n_coarse,
+                     gp_level_stats *stats);
+
+/*
+ * Cluster contraction (Sec. 2): coarse node A weighs the total weight of
+ * its members; coarse edge {A, B}, A != B, weighs the total weight of the
+ * fine edges between the two clusters.  cmap (device, g->n entries) maps to
+ * [0, n_coarse).  *out receives a new graph allocated through the context
+ * allocator (release with gp_graph_release).  Row order inside a coarse row
+ * is unspecified.  Synchronises.
+ */
+gp_status gp_contract(gp_ctx *ctx, const gp_graph *g, const int32_t *cmap, int32_t n_coarse,
+                      gp_graph *out);
+
+/*
+ * Edge sparsification to m_hat edges in expectation (Sec. 4.2).  mode
+ * GP_SPARSIFY_TWEIGHT (weighted threshold sampling): the m_hat-th heaviest
+ * undirected edge weight w_t is found; heavier edges are kept, lighter ones
+ * dropped and edges of weight w_t kept with probability
+ * (m_hat - |E>|) / |E=| by a counter-based hash of their endpoints.
+ * GP_SPARSIFY_UNIFORM keeps every edge with probability m_hat / |E|.  Kept
+ * edges keep their weights; node weights are copied.  *out is allocated
+ * through the context allocator.  `stats` (host, may be NULL) gets w_t,
+ * |E>|, |E=| and the hash threshold in its omega_t / n_greater / n_equal /
+ * threshold fields.  Synchronises.
+ */
+gp_status gp_sparsify(gp_ctx *ctx, const gp_graph *g, int64_t m_hat, int32_t level,
+                      uint64_t seed, int32_t mode, gp_graph *out, gp_level_stats *stats);
+
+/*
+ * Full multilevel partition (Sec. 2, Alg. 1, Sec. 4.3): coarsening with
+ * sparsification, recursive-bisection initial partitioning of the coarsest
+ * graph on the device, and label-propagation refinement on every level.
+ * blocks (device, g->n entries, caller-owned) receives block ids in [0, k);
+ * *cut (host) the cut weight.  eps > 0 is used as round(eps * 1e6) parts
+ * per million.  `stats` (host, may be NULL).  Synchronises.
+ */
+gp_status gp_partition(gp_ctx *ctx, const gp_graph *g, int32_t k, double eps, uint64_t seed,
+                       const gp_config *cfg, int32_t *blocks, int64_t *cut,
+                       gp_partition_stats *stats);
+
+/*
+ * gp_partition on HOST arrays: copies the graph (n + 1 + 2 m2 + n int32
+ * values) to the device, partitions, and copies the n block ids back into
+ * `blocks` (host).  Page-locked host memory makes the copies faster.
+ */
+gp_status gp_partition_host(gp_ctx *ctx, int32_t n, int64_t m2, const int32_t *xadj,
+                            const int32_t *adjncy, const int32_t *vwgt, const int32_t *adjwgt,
+                            int32_t k, double eps, uint64_t seed, const gp_config *cfg,
+                            int32_t *blocks, int64_t *cut, gp_partition_stats *stats);
+
+/* ---- the steps gp_partition is made of (also used by the tests) ---- */
+
+/*
+ * Recursive-bisection initial partition of a small graph (Sec. 4.3): each
+ * bisection runs cfg->ip_trials seeded greedy-growing trials, one thread
+ * block per trial, and keeps the smallest cut.  blocks: device, n entries.
+ */
+gp_status gp_initial_partition(gp_ctx *ctx, const gp_graph *g, int32_t k, double eps,
+                               uint64_t seed, const gp_config *cfg, int32_t *blocks);
+
+/* Moves nodes out of blocks heavier than Lmax (greedy, least cut loss). */
+gp_status gp_rebalance(gp_ctx *ctx, const gp_graph *g, int32_t k, int64_t Lmax,
+                       int32_t *blocks, int64_t *moves);
+
+/*
+ * Size-constrained label-propagation refinement (Sec. 3): blocks are the
+ * labels, Lmax the bound; cfg->ref_rounds rounds of strictly improving
+ * moves.  blocks: device, in/out.  *moves (host, may be NULL).
+ */
+gp_status gp_refine(gp_ctx *ctx, const gp_graph *g, int32_t k, int64_t Lmax, int32_t level,
+                    uint64_t seed, const gp_config *cfg, int32_t *blocks, int64_t *moves);
+
+/* Projection (uncoarsening): fine[v] = coarse[cmap[v]] for v < n. Device arrays. */
+gp_status gp_project(gp_ctx *ctx, int32_t n, const int32_t *cmap, const int32_t *coarse,
+                     int32_t *fine);
+
+/*
+ * Cut weight and block weights of a partition (Sec. 2).  block_weights:
+ * host array of k entries, may be NULL.  Synchronises.
+ */
+gp_status gp_cut(gp_ctx *ctx, const gp_graph *g, const int32_t *blocks, int32_t k, int64_t *cut,
+                 int64_t *block_weights);
+
+/* Frees a graph returned by gp_contract / gp_sparsify. */
+void gp_graph_release(gp_ctx *ctx, gp_graph *g);
+
+/*
+ * Profiling: when enabled, every major kernel launch is bracketed by CUDA
+ * events on the context stream, and gp_profile_read returns, per kernel
+ * class, the launch count, the summed device time (ms) and the algorithmic
+ * bytes moved (the per-unit figures of the design document).  Classes are
+ * named by gp_profile_name(i) for i < gp_profile_count().
+ */
+void gp_profile_enable(gp_ctx *ctx, int on);
+void gp_profile_reset(gp_ctx *ctx);
+int gp_profile_count(void);
+const char *gp_profile_name(int i);
+gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H */

@@ -1,0 +1,760 @@
+// lp.cu -- size-constrained label propagation (Sec. 3 of the paper; the
+// clustering of Sec. 4.1 and the refinement of Sec. 4.3) as synchronous
+// sub-rounds with hash priorities:
+//
+//  per round r: nodes with neighbours are bucketed by (sub-round, degree
+//  class); per sub-round s:
+//   rate   : every active node sums the edge weight to each neighbouring
+//            label on the snapshot and picks the admissible label of largest
+//            rating (ties: smallest h32(TIE), then smallest label); it
+//            proposes when that beats its own label's rating
+//   decide : a target whose snapshot weight plus all incoming weight fits
+//            the bound accepts everybody; the proposers of overflowing
+//            targets are sorted by (target, h32(PRIO), node) and accepted
+//            while the running weight fits (longest prefix)
+//   apply  : labels, weights and cluster sizes are updated; emptied
+//            clusters are counted; the stop flag is raised when the cluster
+//            count reaches n_min or a round moved nothing.
+#include "lp.cuh"
+
+namespace gp {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int kMedSlots = 256;
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kMaxKeys = 64 * kNumBuckets;
+
+struct RateArgs {
+  const int32_t *xadj, *adjncy, *adjwgt, *vwgt, *label, *weight;
+  const int32_t *list;
+  const int32_t *offs;
+  int key;
+  int64_t bound;
+  uint64_t ktie;
+  int32_t *target;      // RATE_LP: per node proposal (-1 none)
+  int32_t *incoming;    // RATE_LP: per label incoming weight
+  uint64_t *fav_keys;   // RATE_FAV: per list position (fav << 32 | v)
+  const int *stop;
+  int32_t *gkeys, *gvals;  // large kernel global tables
+  int64_t gstride;
+  unsigned long long *units;
+};
+
+__device__ __forceinline__ void add_units(unsigned long long *units, unsigned long long e,
+                                          unsigned long long v, unsigned long long c,
+                                          unsigned long long p) {
+  if (!units) return;
+  e = warp_sum(e); v = warp_sum(v); c = warp_sum(c); p = warp_sum(p);
+  if (lane_id() == 0) {
+    if (e) atomicAdd(units + 0, e);
+    if (v) atomicAdd(units + 1, v);
+    if (c) atomicAdd(units + 2, c);
+    if (p) atomicAdd(units + 3, p);
+  }
+}
+
+__device__ __forceinline__ unsigned slot_hash(int L, int bits) {
+  return ((unsigned)L * 2654435761u) >> (32 - bits);
+}
+
+template <int MODE>
+__device__ __forceinline__ void emit(const RateArgs &a, int i, int v, int best, int cv) {
+  if (MODE == RATE_LP) {
+    a.target[v] = best;
+    atomicAdd(&a.incoming[best], cv);
+  } else {
+    a.fav_keys[i] = ((uint64_t)(uint32_t)best << 32) | (uint32_t)v;
+  }
+}
+
+// ------------------------------------------------ degree <= 32: warp/node
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_rate_small(RateArgs a) {
+  if (a.stop && *a.stop) return;
+  const int begin = a.offs[a.key], end = a.offs[a.key + 1];
+  const int lane = (int)lane_id();
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
+  for (int i = begin + wid; i < end; i += nw) {
+    const int v = a.list[i];
+    const int start = a.xadj[v];
+    const int deg = a.xadj[v + 1] - start;
+    const int own = a.label[v];
+    const int cv = a.vwgt[v];
+    const bool valid = lane < deg;
+    int L = 0, w = 0;
+    if (valid) {
+      L = a.label[a.adjncy[start + lane]];
+      w = a.adjwgt[start + lane];
+    }
+    const unsigned key = valid ? (unsigned)L : (0x80000000u | (unsigned)lane);
+    const unsigned peers = __match_any_sync(FULL, key);
+    const int sum = __reduce_add_sync(peers, w);
+    const bool leader = valid && lane == __ffs(peers) - 1;
+    const int own_r = __reduce_max_sync(FULL, (leader && L == own) ? sum : 0);
+    bool cand = leader && L != own;
+    const unsigned ncand = __popc(__ballot_sync(FULL, cand));
+    if (MODE == RATE_LP && cand) cand = (int64_t)a.weight[L] + cv <= a.bound;
+    const int rmax = __reduce_max_sync(FULL, cand ? sum : -1);
+    ue += deg; uv += 1; uc += ncand;
+    if (rmax < 0 || (MODE == RATE_LP && rmax <= own_r)) continue;
+    const bool top = cand && sum == rmax;
+    const unsigned h = top ? h32(a.ktie, (uint32_t)v, (uint32_t)L) : 0xFFFFFFFFu;
+    const unsigned hmin = __reduce_min_sync(FULL, h);
+    const unsigned best = __reduce_min_sync(FULL, (top && h == hmin) ? (unsigned)L : 0xFFFFFFFFu);
+    if (lane == 0) emit<MODE>(a, i, v, (int)best, cv);
+    up += 1;
+  }
+  add_units(a.units, lane == 0 ? ue : 0, lane == 0 ? uv : 0, lane == 0 ? uc : 0, lane == 0 ? up : 0);
+}
+
+// --------------------------------------- degree <= 128: warp/node + table
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
+  __shared__ int s_k[kWarpsPerBlock][kMedSlots];
+  __shared__ int s_v[kWarpsPerBlock][kMedSlots];
+  const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+  int *tk = s_k[wib], *tv = s_v[wib];
+  for (int t = lane; t < kMedSlots; t += 32) { tk[t] = -1; tv[t] = 0; }
+  __syncwarp();
+  if (a.stop && *a.stop) return;
+  const int begin = a.offs[a.key], end = a.offs[a.key + 1];
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
+  for (int i = begin + wid; i < end; i += nw) {
+    const int v = a.list[i];
+    const int start = a.xadj[v];
+    const int deg = a.xadj[v + 1] - start;
+    const int own = a.label[v];
+    const int cv = a.vwgt[v];
+    for (int j = lane; j < deg; j += 32) {
+      const int L = a.label[a.adjncy[start + j]];
+      const int w = a.adjwgt[start + j];
+      unsigned s = slot_hash(L, 8);
+      for (int probe = 0; probe < kMedSlots; probe++) {  // bounded: the table never fills
+        const int prev = atomicCAS(&tk[s], -1, L);
+        if (prev == -1 || prev == L) { atomicAdd(&tv[s], w); break; }
+        s = (s + 1) & (kMedSlots - 1);
+      }
+    }
+    __syncwarp();
+    int own_loc = 0, rloc = -1, nc = 0;
+    for (int t = lane; t < kMedSlots; t += 32) {
+      const int L = tk[t];
+      if (L < 0) continue;
+      const int r = tv[t];
+      if (L == own) { own_loc = r; continue; }
+      nc++;
+      if (MODE == RATE_LP && (int64_t)a.weight[L] + cv > a.bound) continue;
+      rloc = r > rloc ? r : rloc;
+    }
+    const int own_r = warp_max(own_loc);
+    const int rmax = warp_max(rloc);
+    ue += deg; uv += 1; uc += nc;
+    if (!(rmax < 0 || (MODE == RATE_LP && rmax <= own_r))) {
+      uint64_t packed = ~0ull;
+      for (int t = lane; t < kMedSlots; t += 32) {
+        const int L = tk[t];
+        if (L < 0 || L == own || tv[t] != rmax) continue;
+        if (MODE == RATE_LP && (int64_t)a.weight[L] + cv > a.bound) continue;
+        const uint64_t p = ((uint64_t)h32(a.ktie, (uint32_t)v, (uint32_t)L) << 32) | (uint32_t)L;
+        packed = p < packed ? p : packed;
+      }
+      packed = warp_min(packed);
+      if (lane == 0) { emit<MODE>(a, i, v, (int)(uint32_t)packed, cv); up += 1; }
+    }
+    for (int t = lane; t < kMedSlots; t += 32) { tk[t] = -1; tv[t] = 0; }
+    __syncwarp();
+  }
+  add_units(a.units, ue * (lane == 0), uv * (lane == 0), uc, up);
+}
+
+// --------------------------------------------- degree > 128: block/node
+
+__device__ __forceinline__ int block_max_i32(int v, int *s_red) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane_id() == 0) s_red[w] = v;
+  __syncthreads();
+  int r = s_red[0];
+  for (int i = 1; i < kWarpsPerBlock; i++) r = s_red[i] > r ? s_red[i] : r;
+  return r;
+}
+
+__device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t *s_red) {
+  v = warp_min(v);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane_id() == 0) s_red[w] = v;
+  __syncthreads();
+  uint64_t r = s_red[0];
+  for (int i = 1; i < kWarpsPerBlock; i++) r = s_red[i] < r ? s_red[i] : r;
+  return r;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
+  __shared__ int s_k[kLargeSmemSlots];
+  __shared__ int s_v[kLargeSmemSlots];
+  __shared__ int s_ri[kWarpsPerBlock];
+  __shared__ uint64_t s_ru[kWarpsPerBlock];
+  if (a.stop && *a.stop) return;
+  for (int t = threadIdx.x; t < kLargeSmemSlots; t += blockDim.x) { s_k[t] = -1; s_v[t] = 0; }
+  __syncthreads();
+  const int begin = a.offs[a.key], end = a.offs[a.key + 1];
+  int *gk = a.gkeys ? a.gkeys + (int64_t)blockIdx.x * a.gstride : nullptr;
+  int *gv = a.gvals ? a.gvals + (int64_t)blockIdx.x * a.gstride : nullptr;
+  unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
+  for (int i = begin + (int)blockIdx.x; i < end; i += (int)gridDim.x) {
+    const int v = a.list[i];
+    const int start = a.xadj[v];
+    const int deg = a.xadj[v + 1] - start;
+    const int own = a.label[v];
+    const int cv = a.vwgt[v];
+    int bits = 1;
+    while ((1 << bits) < 2 * deg) bits++;
+    const int tsize = 1 << bits;
+    const bool in_smem = tsize <= kLargeSmemSlots;
+    int *tk = in_smem ? s_k : gk;
+    int *tv = in_smem ? s_v : gv;
+    for (int j = threadIdx.x; j < deg; j += blockDim.x) {
+      const int L = a.label[a.adjncy[start + j]];
+      const int w = a.adjwgt[start + j];
+      unsigned s = slot_hash(L, bits);
+      for (int probe = 0; probe < tsize; probe++) {  // bounded: the table never fills
+        const int prev = atomicCAS(&tk[s], -1, L);
+        if (prev == -1 || prev == L) { atomicAdd(&tv[s], w); break; }
+        s = (s + 1) & (unsigned)(tsize - 1);
+      }
+    }
+    __syncthreads();
+    int own_loc = 0, rloc = -1, nc = 0;
+    for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
+      const int L = tk[t];
+      if (L < 0) continue;
+      const int r = tv[t];
+      if (L == own) { own_loc = r; continue; }
+      nc++;
+      if (MODE == RATE_LP && (int64_t)a.weight[L] + cv > a.bound) continue;
+      rloc = r > rloc ? r : rloc;
+    }
+    const int own_r = block_max_i32(own_loc, s_ri);
+    const int rmax = block_max_i32(rloc, s_ri);
+    uc += nc;
+    if (threadIdx.x == 0) { ue += deg; uv += 1; }
+    if (!(rmax < 0 || (MODE == RATE_LP && rmax <= own_r))) {
+      uint64_t packed = ~0ull;
+      for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
+        const int L = tk[t];
+        if (L < 0 || L == own || tv[t] != rmax) continue;
+        if (MODE == RATE_LP && (int64_t)a.weight[L] + cv > a.bound) continue;
+        const uint64_t p = ((uint64_t)h32(a.ktie, (uint32_t)v, (uint32_t)L) << 32) | (uint32_t)L;
+        packed = p < packed ? p : packed;
+      }
+      packed = block_min_u64(packed, s_ru);
+      if (threadIdx.x == 0) { emit<MODE>(a, i, v, (int)(uint32_t)packed, cv); up += 1; }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tsize; t += blockDim.x) { tk[t] = -1; tv[t] = 0; }
+    __syncthreads();
+  }
+  add_units(a.units, ue, uv, uc, up);
+}
+
+// ----------------------------------------------------- per-round buckets
+
+struct BucketArgs {
+  const int32_t *xadj, *label, *size, *vwgt;
+  int n;
+  uint64_t kact;
+  int S;           // sub-rounds (1 for the favourite lists)
+  int fav_mode;    // 0: all nodes with neighbours; 1: light singletons
+  int64_t U;       // fav_mode: light means 2 c <= U
+  const int *stop;
+};
+
+__device__ __forceinline__ int bucket_key(const BucketArgs &b, int v) {
+  const int deg = b.xadj[v + 1] - b.xadj[v];
+  if (deg == 0) return -1;
+  if (b.fav_mode) {
+    if (b.size[b.label[v]] != 1 || 2 * (int64_t)b.vwgt[v] > b.U) return -1;
+    return degree_bucket(deg);
+  }
+  const int s = (int)(h32(b.kact, (uint32_t)v, 0) % (uint32_t)b.S);
+  return s * kNumBuckets + degree_bucket(deg);
+}
+
+constexpr int kChunk = kThreads * 16;
+
+__global__ void __launch_bounds__(kThreads) k_bucket_count(BucketArgs b, int nkeys, int *cnt) {
+  __shared__ int s_c[kMaxKeys];
+  if (b.stop && *b.stop) return;
+  for (int t = threadIdx.x; t < nkeys; t += blockDim.x) s_c[t] = 0;
+  __syncthreads();
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < b.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int k = bucket_key(b, (int)v);
+    if (k >= 0) atomicAdd(&s_c[k], 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nkeys; t += blockDim.x)
+    if (s_c[t]) atomicAdd(&cnt[t], s_c[t]);
+}
+
+__global__ void k_bucket_offsets(const int *cnt, int nkeys, int *offs, int *cursor, const int *stop) {
+  if (stop && *stop) return;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < nkeys; k++) {
+      offs[k] = run;
+      cursor[k] = run;
+      run += cnt[k];
+    }
+    offs[nkeys] = run;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bucket_scatter(BucketArgs b, int nkeys, int *cursor,
+                                                             int32_t *list) {
+  __shared__ int s_c[kMaxKeys];
+  __shared__ int s_base[kMaxKeys];
+  if (b.stop && *b.stop) return;
+  for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < b.n; c0 += (int64_t)gridDim.x * kChunk) {
+    for (int t = threadIdx.x; t < nkeys; t += blockDim.x) s_c[t] = 0;
+    __syncthreads();
+    int keys[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+      const int64_t v = c0 + j * kThreads + threadIdx.x;
+      keys[j] = v < b.n ? bucket_key(b, (int)v) : -1;
+      if (keys[j] >= 0) atomicAdd(&s_c[keys[j]], 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nkeys; t += blockDim.x) {
+      s_base[t] = s_c[t] ? atomicAdd(&cursor[t], s_c[t]) : 0;
+      s_c[t] = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+      if (keys[j] < 0) continue;
+      const int64_t v = c0 + j * kThreads + threadIdx.x;
+      const int pos = s_base[keys[j]] + atomicAdd(&s_c[keys[j]], 1);
+      list[pos] = (int32_t)v;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- acceptance
+
+struct Counters {
+  int stop;
+  int nov;
+  long long moved_sub;
+  long long moved_round;
+  long long moved_total;
+  long long emptied;
+  long long nclusters;
+  long long pad;
+};
+
+__global__ void __launch_bounds__(kThreads) k_decide(const int32_t *list, const int32_t *offs,
+                                                     int k0, int k1, const int32_t *target,
+                                                     const int32_t *vwgt, const int32_t *weight,
+                                                     const int32_t *incoming, int64_t bound,
+                                                     uint8_t *acc, uint64_t *ov_key,
+                                                     uint32_t *ov_val, Counters *cnt, uint64_t kprio) {
+  if (cnt->stop) return;
+  const int begin = offs[k0], end = offs[k1];
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += stride) {
+    const int i = base + (int)threadIdx.x;
+    bool over = false;
+    int v = 0, K = 0;
+    if (i < end) {
+      v = list[i];
+      K = target[v];
+      if (K >= 0) {
+        if ((int64_t)weight[K] + incoming[K] <= bound) acc[v] = 1;
+        else over = true;
+      }
+    }
+    const int pos = warp_append(&cnt->nov, over);
+    if (over) {
+      ov_key[pos] = ((uint64_t)(uint32_t)K << 32) | h32(kprio, (uint32_t)v, 0);
+      ov_val[pos] = (uint32_t)v;
+    }
+  }
+}
+
+// Runs of equal keys are ordered by node id (the last tie-break of R7).
+__global__ void k_fix_runs(const uint64_t *keys, uint32_t *vals, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i > 0 && keys[i - 1] == keys[i]) continue;
+    if (i + 1 >= n || keys[i + 1] != keys[i]) continue;
+    int e = i + 1;
+    while (e < n && keys[e] == keys[i]) e++;
+    for (int a = i + 1; a < e; a++) {
+      uint32_t x = vals[a];
+      int b = a - 1;
+      while (b >= i && vals[b] > x) { vals[b + 1] = vals[b]; b--; }
+      vals[b + 1] = x;
+    }
+  }
+}
+
+__global__ void k_ov_weights(const uint32_t *vals, int n, const int32_t *vwgt, int64_t *cs) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    cs[i] = vwgt[vals[i]];
+}
+
+__global__ void k_ov_accept(const uint64_t *keys, const uint32_t *vals, int n, const int64_t *ps,
+                            const int32_t *vwgt, const int32_t *weight, int64_t bound, uint8_t *acc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    const uint64_t seg = k & 0xFFFFFFFF00000000ull;
+    int lo = 0, hi = i;  // first index with key >= seg
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (keys[mid] < seg) lo = mid + 1; else hi = mid;
+    }
+    const int K = (int)(k >> 32);
+    const int64_t incl = ps[i] - ps[lo] + vwgt[vals[i]];
+    acc[vals[i]] = (int64_t)weight[K] + incl <= bound ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply(const int32_t *list, const int32_t *offs, int k0,
+                                                    int k1, const int32_t *target, uint8_t *acc,
+                                                    const int32_t *vwgt, int32_t *label,
+                                                    int32_t *weight, int32_t *size,
+                                                    int32_t *leave_cnt, int32_t *first_own,
+                                                    Counters *cnt, int agg_weights) {
+  if (cnt->stop) return;
+  const int begin = offs[k0], end = offs[k1];
+  const int stride = gridDim.x * blockDim.x;
+  long long moved = 0;
+  for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += stride) {
+    const int i = base + (int)threadIdx.x;
+    bool mv = false;
+    int v = 0, K = 0, own = 0, c = 0;
+    if (i < end) {
+      v = list[i];
+      K = target[v];
+      mv = K >= 0 && acc[v] == 1;
+      if (mv) {
+        own = label[v];
+        c = vwgt[v];
+        label[v] = K;
+        if (size) {
+          atomicAdd(&size[K], 1);
+          atomicSub(&size[own], 1);
+          if (atomicAdd(&leave_cnt[own], 1) == 0) {
+            acc[v] = 2;
+            first_own[v] = own;
+          }
+        }
+      }
+    }
+    if (agg_weights) {
+      warp_agg_add(weight, K, c, mv);
+      warp_agg_add(weight, own, -c, mv);
+    } else if (mv) {
+      atomicAdd(&weight[K], c);
+      atomicSub(&weight[own], c);
+    }
+    moved += mv;
+  }
+  moved = warp_sum(moved);
+  if (lane_id() == 0 && moved)
+    atomicAdd((unsigned long long *)&cnt->moved_sub, (unsigned long long)moved);
+}
+
+__global__ void __launch_bounds__(kThreads) k_finalize(const int32_t *list, const int32_t *offs,
+                                                       int k0, int k1, int32_t *target,
+                                                       uint8_t *acc, int32_t *incoming,
+                                                       const int32_t *size, int32_t *leave_cnt,
+                                                       const int32_t *first_own, Counters *cnt) {
+  if (cnt->stop) return;
+  const int begin = offs[k0], end = offs[k1];
+  long long emptied = 0;
+  for (int i = begin + blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
+    const int v = list[i];
+    const int K = target[v];
+    if (K < 0) continue;
+    incoming[K] = 0;
+    if (acc[v] == 2) {
+      const int own = first_own[v];
+      if (size[own] == 0) emptied++;
+      leave_cnt[own] = 0;
+    }
+    target[v] = -1;
+    acc[v] = 0;
+  }
+  emptied = warp_sum(emptied);
+  if (lane_id() == 0 && emptied)
+    atomicAdd((unsigned long long *)&cnt->emptied, (unsigned long long)emptied);
+}
+
+__global__ void k_subround_end(Counters *cnt, int count_clusters, long long n_min) {
+  if (cnt->stop) return;
+  cnt->nclusters -= cnt->emptied;
+  cnt->emptied = 0;
+  cnt->moved_round += cnt->moved_sub;
+  cnt->moved_total += cnt->moved_sub;
+  cnt->moved_sub = 0;
+  if (count_clusters && cnt->nclusters <= n_min) cnt->stop = 1;
+}
+
+__global__ void k_round_end(Counters *cnt) {
+  if (cnt->stop) return;
+  if (cnt->moved_round == 0) cnt->stop = 1;
+  cnt->moved_round = 0;
+}
+
+__global__ void k_counters_init(Counters *cnt, long long nclusters) {
+  cnt->stop = 0; cnt->nov = 0; cnt->moved_sub = 0; cnt->moved_round = 0; cnt->moved_total = 0;
+  cnt->emptied = 0; cnt->nclusters = nclusters; cnt->pad = 0;
+}
+
+__global__ void k_reset_nov(Counters *cnt) { cnt->nov = 0; }
+
+__global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+// Largest degree among nodes with more than kMediumMaxDeg neighbours.
+__global__ void k_max_degree(const int32_t *xadj, int n, int *out) {
+  int m = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int d = xadj[v + 1] - xadj[v];
+    m = d > m ? d : m;
+  }
+  m = warp_max(m);
+  if (lane_id() == 0 && m) atomicMax(out, m);
+}
+
+struct RateTables {
+  DBuf<int32_t> gkeys, gvals;
+  int64_t stride = 0;
+  int blocks = 0;
+};
+
+// Global hash tables for the block-per-node kernel when some node needs more
+// than kLargeSmemSlots slots.
+void make_tables(gp_ctx *ctx, const DevGraph &g, RateTables &t) {
+  DBuf<int> md(ctx, 1);
+  md.zero();
+  k_max_degree<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(g.xadj, g.n, md.get());
+  GP_LAUNCH_CHECK();
+  const int maxdeg = read_scalar(ctx, md.get());
+  int bits = 1;
+  while ((1 << bits) < 2 * maxdeg) bits++;
+  t.blocks = ctx->num_sms * 4;
+  if ((1 << bits) > kLargeSmemSlots) {
+    t.stride = (int64_t)1 << bits;
+    t.gkeys.reset(ctx, (size_t)(t.stride * t.blocks));
+    t.gvals.reset(ctx, (size_t)(t.stride * t.blocks));
+    t.gkeys.fill_bytes(0xFF);
+    t.gvals.zero();
+  }
+}
+
+template <int MODE>
+void launch_rate(gp_ctx *ctx, RateArgs a, int bucket_key_base, const RateTables &t) {
+  const int grid_w = ctx->num_sms * 8;
+  a.key = bucket_key_base + 0;
+  k_rate_small<MODE><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  GP_LAUNCH_CHECK();
+  a.key = bucket_key_base + 1;
+  k_rate_medium<MODE><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  GP_LAUNCH_CHECK();
+  a.key = bucket_key_base + 2;
+  a.gkeys = t.gkeys.get();
+  a.gvals = t.gvals.get();
+  a.gstride = t.stride;
+  k_rate_large<MODE><<<t.blocks, kThreads, 0, ctx->stream>>>(a);
+  GP_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+int bits_for(int64_t x) {
+  int b = 0;
+  while (((int64_t)1 << b) <= x) b++;
+  return b < 1 ? 1 : b;
+}
+
+LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int32_t *size,
+                int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev) {
+  LpResult res;
+  const int n = g.n;
+  const int S = p.subrounds;
+  GP_REQUIRE(S >= 1 && S <= 64, GP_ERR_INVALID, "lp_subrounds must be in [1, 64]");
+  const int nkeys = S * kNumBuckets;
+  DBuf<int32_t> list(ctx, (size_t)n), target(ctx, (size_t)n), incoming(ctx, (size_t)nlabels);
+  DBuf<uint8_t> acc(ctx, (size_t)n);
+  DBuf<int32_t> cnt(ctx, (size_t)nkeys), offs(ctx, (size_t)nkeys + 1), cursor(ctx, (size_t)nkeys);
+  DBuf<uint64_t> ov_key(ctx, (size_t)n);
+  DBuf<uint32_t> ov_val(ctx, (size_t)n);
+  DBuf<int32_t> leave_cnt, first_own;
+  if (size) {
+    leave_cnt.reset(ctx, (size_t)nlabels);
+    leave_cnt.zero();
+    first_own.reset(ctx, (size_t)n);
+  }
+  DBuf<Counters> counters(ctx, 1);
+  Counters *C = counters.get();
+  k_fill_i32<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(target.get(), n, -1);
+  GP_LAUNCH_CHECK();
+  acc.zero();
+  incoming.zero();
+  int64_t ncl0 = 0;
+  if (p.count_clusters && nclusters_dev) read_back(ctx, nclusters_dev, sizeof(int64_t), &ncl0);
+  k_counters_init<<<1, 1, 0, ctx->stream>>>(C, ncl0);
+  GP_LAUNCH_CHECK();
+  RateTables tables;
+  make_tables(ctx, g, tables);
+  unsigned long long *units_rate = ctx->d_units ? ctx->d_units + p.prof_rate * PROF_UNITS : nullptr;
+
+  const int grid = ctx->num_sms * 8;
+  const bool agg = nlabels <= 4096;  // refinement: few labels, aggregate weight updates
+  bool stop = n == 0 || (p.count_clusters && ncl0 <= p.n_min);
+  int32_t subs = 0;
+  for (int r = 0; r < p.rounds && !stop; r++) {
+    const uint64_t kact = stream_key(seed, p.tag_act, (uint32_t)p.level, (uint32_t)r);
+    const uint64_t ktie = stream_key(seed, p.tag_tie, (uint32_t)p.level, (uint32_t)r);
+    const uint64_t kprio = stream_key(seed, p.tag_prio, (uint32_t)p.level, (uint32_t)r);
+    {
+      ProfScope ps(ctx, PROF_ROUND_SETUP);
+      BucketArgs b{g.xadj, label, size, g.vwgt, n, kact, S, 0, 0, &C->stop};
+      cnt.zero();
+      k_bucket_count<<<grid_for(n, kThreads, grid), kThreads, 0, ctx->stream>>>(b, nkeys, cnt.get());
+      GP_LAUNCH_CHECK();
+      k_bucket_offsets<<<1, 1, 0, ctx->stream>>>(cnt.get(), nkeys, offs.get(), cursor.get(), &C->stop);
+      GP_LAUNCH_CHECK();
+      k_bucket_scatter<<<grid_for(n, kChunk, grid), kThreads, 0, ctx->stream>>>(b, nkeys, cursor.get(),
+                                                                               list.get());
+      GP_LAUNCH_CHECK();
+    }
+    for (int s = 0; s < S; s++) {
+      if (p.dbg_max_subrounds >= 0 && subs >= p.dbg_max_subrounds) { stop = true; break; }
+      RateArgs a{};
+      a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
+      a.label = label; a.weight = weight; a.list = list.get(); a.offs = offs.get();
+      a.bound = p.bound; a.ktie = ktie; a.target = target.get(); a.incoming = incoming.get();
+      a.stop = &C->stop; a.units = units_rate;
+      {
+        ProfScope ps(ctx, p.prof_rate);
+        launch_rate<RATE_LP>(ctx, a, s * kNumBuckets, tables);
+      }
+      const int k0 = s * kNumBuckets, k1 = s * kNumBuckets + kNumBuckets;
+      int nov = 0;
+      {
+        ProfScope ps(ctx, p.prof_accept);
+        k_reset_nov<<<1, 1, 0, ctx->stream>>>(C);
+        k_decide<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(),
+                                                      g.vwgt, weight, incoming.get(), p.bound,
+                                                      acc.get(), ov_key.get(), ov_val.get(), C, kprio);
+        GP_LAUNCH_CHECK();
+      }
+      int hdr[2];
+      read_back(ctx, C, sizeof(hdr), hdr);
+      if (hdr[0]) { stop = true; break; }
+      nov = hdr[1];
+      subs++;
+      if (nov > 0) {
+        ProfScope ps(ctx, p.prof_accept);
+        const int kbits = bits_for(nlabels) + 32;
+        radix_sort_pairs(ctx, ov_key.get(), ov_val.get(), nov, kbits);
+        const int gsmall = grid_for(nov, 256, grid);
+        k_fix_runs<<<gsmall, 256, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov);
+        DBuf<int64_t> cs(ctx, (size_t)nov);
+        k_ov_weights<<<gsmall, 256, 0, ctx->stream>>>(ov_val.get(), nov, g.vwgt, cs.get());
+        scan_exclusive_i64(ctx, cs.get(), cs.get(), nov, nullptr);
+        k_ov_accept<<<gsmall, 256, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov, cs.get(), g.vwgt,
+                                                     weight, p.bound, acc.get());
+        GP_LAUNCH_CHECK();
+      }
+      {
+        ProfScope ps(ctx, p.prof_accept);
+        k_apply<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(),
+                                                     acc.get(), g.vwgt, label, weight, size,
+                                                     leave_cnt.get(), first_own.get(), C, agg ? 1 : 0);
+        GP_LAUNCH_CHECK();
+        k_finalize<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(),
+                                                        acc.get(), incoming.get(), size,
+                                                        leave_cnt.get(), first_own.get(), C);
+        GP_LAUNCH_CHECK();
+        k_subround_end<<<1, 1, 0, ctx->stream>>>(C, p.count_clusters ? 1 : 0, (long long)p.n_min);
+        GP_LAUNCH_CHECK();
+      }
+    }
+    if (stop) break;
+    k_round_end<<<1, 1, 0, ctx->stream>>>(C);
+    GP_LAUNCH_CHECK();
+  }
+  Counters hc;
+  read_back(ctx, C, sizeof(Counters), &hc);
+  res.subrounds = subs;
+  res.moves = hc.moved_total;
+  res.nclusters = hc.nclusters;
+  if (p.count_clusters && nclusters_dev)
+    GP_CUDA(cudaMemcpyAsync(nclusters_dev, &C->nclusters, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  return res;
+}
+
+// ------------------------------------------------------- 2-hop favourites
+
+namespace {
+__global__ void k_fill_u64(uint64_t *a, int64_t n, uint64_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+}  // namespace
+
+void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, const int32_t *size,
+                         int64_t U, uint64_t kfav, DBuf<uint64_t> &keys, int32_t &count) {
+  const int n = g.n;
+  const int nkeys = kNumBuckets;
+  const int grid = ctx->num_sms * 8;
+  DBuf<int32_t> list(ctx, (size_t)n), cnt(ctx, (size_t)nkeys), offs(ctx, (size_t)nkeys + 1),
+      cursor(ctx, (size_t)nkeys);
+  BucketArgs b{g.xadj, label, size, g.vwgt, n, 0, 1, 1, U, nullptr};
+  cnt.zero();
+  k_bucket_count<<<grid_for(n, kThreads, grid), kThreads, 0, ctx->stream>>>(b, nkeys, cnt.get());
+  GP_LAUNCH_CHECK();
+  k_bucket_offsets<<<1, 1, 0, ctx->stream>>>(cnt.get(), nkeys, offs.get(), cursor.get(), nullptr);
+  k_bucket_scatter<<<grid_for(n, kChunk, grid), kThreads, 0, ctx->stream>>>(b, nkeys, cursor.get(),
+                                                                           list.get());
+  GP_LAUNCH_CHECK();
+  int32_t total = 0;
+  read_back(ctx, offs.get() + nkeys, sizeof(int32_t), &total);
+  count = total;
+  keys.reset(ctx, (size_t)(total > 0 ? total : 1));
+  if (total == 0) return;
+  k_fill_u64<<<grid_for(total, 256, grid), 256, 0, ctx->stream>>>(keys.get(), total, ~0ull);
+  RateTables tables;
+  make_tables(ctx, g, tables);
+  RateArgs a{};
+  a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
+  a.label = label; a.weight = nullptr; a.list = list.get(); a.offs = offs.get();
+  a.bound = U; a.ktie = kfav; a.fav_keys = keys.get(); a.stop = nullptr;
+  launch_rate<RATE_FAV>(ctx, a, 0, tables);
+}
+
+}  // namespace gp

@@ -1,0 +1,52 @@
+// lp.cuh -- size-constrained label propagation on the GPU (shared by
+// clustering, refinement and the 2-hop favourite search).
+#pragma once
+#include "gp_internal.cuh"
+
+namespace gp {
+
+// Degree classes of the rating kernels.
+constexpr int kNumBuckets = 3;
+constexpr int kSmallMaxDeg = 32;    // one warp, one neighbour per lane
+constexpr int kMediumMaxDeg = 128;  // one warp, shared-memory table of 256 slots
+constexpr int kLargeSmemSlots = 4096;  // one block; bigger tables live in global memory
+
+__host__ __device__ __forceinline__ int degree_bucket(int deg) {
+  return deg <= kSmallMaxDeg ? 0 : (deg <= kMediumMaxDeg ? 1 : 2);
+}
+
+enum RateMode { RATE_LP = 0, RATE_FAV = 1 };
+
+struct LpParams {
+  uint32_t tag_act, tag_tie, tag_prio;
+  int32_t level, rounds, subrounds;
+  int64_t bound;
+  bool count_clusters;
+  int64_t n_min;
+  int32_t dbg_max_subrounds;
+  int prof_rate, prof_accept;
+};
+
+struct LpResult {
+  int32_t subrounds = 0;
+  int64_t moves = 0;
+  int64_t nclusters = 0;
+};
+
+// Runs LP on g.  label (n) and weight (nlabels) are updated in place; size
+// (nlabels) is maintained when p.count_clusters (may be null otherwise).
+// nclusters_dev: device int64 with the current number of non-empty clusters
+// (clustering only).
+LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int32_t *size,
+                int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev);
+
+// 2-hop favourites (Sec. 4.1): for every light singleton (deg > 0, alone in
+// its cluster, 2 c <= U), the adjacent cluster K != label(v) of largest
+// rating, ties by the smallest h32(kfav, v, K) then the smallest K, ignoring
+// U.  keys receives (fav << 32 | v) per singleton; count their number.
+void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, const int32_t *size,
+                         int64_t U, uint64_t kfav, DBuf<uint64_t> &keys, int32_t &count);
+
+int bits_for(int64_t x);
+
+}  // namespace gp

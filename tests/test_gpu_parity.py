@@ -1,0 +1,350 @@
+"""GPU (C-ABI) vs CPU oracle parity, element by element.
+
+Integer work with a fixed deterministic schedule: every comparison is exact
+(tolerance 0).  Coarse rows come back from the GPU in unspecified order, so
+graphs are compared row by row after sorting each row.  Inputs are chosen to
+exercise every kernel variant: degrees <= 32 (warp, one neighbour per lane),
+33..128 (warp hash table), 129..2048 (block, shared table), > 2048 (block,
+global table), isolated nodes, node and edge weights, several tiles and
+ragged tails.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as orc
+from tests._util import clique, hand, matching, star
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+    import paper_2504_17615_gb300 as gpmod
+    from paper_2504_17615_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return gpmod
+
+
+@pytest.fixture(scope="module")
+def ctx(gp):
+    c = gp.Context(0)
+    yield c
+    c.close()
+
+
+def _graphs():
+    return {
+        "er": gg.er(3000, 15000, 1),
+        "er_w": gg.with_node_weights(gg.with_edge_weights(gg.er(5000, 40000, 2), 7), 3),
+        "rmat12": gg.rmat(12, 8, seed=3),
+        "grid": gg.grid2d(60, 50),
+        "star": star(3000),
+        "matching": matching(2000),
+        "iso": gg.with_isolated(gg.er(2000, 6000, 4), 700),
+        "dense": gg.er(600, 60000, 5),
+    }
+
+
+GRAPHS = _graphs()
+
+
+def canon(g):
+    """(xadj, rows sorted) as numpy arrays for exact comparison."""
+    xadj = np.asarray(g.xadj, dtype=np.int64)
+    adj = np.asarray(g.adjncy, dtype=np.int64).copy()
+    w = np.asarray(g.adjwgt, dtype=np.int64).copy()
+    for v in range(g.n):
+        a, b = xadj[v], xadj[v + 1]
+        if b - a > 1:
+            o = np.argsort(adj[a:b], kind="stable")
+            adj[a:b] = adj[a:b][o]
+            w[a:b] = w[a:b][o]
+    return xadj, adj, w, np.asarray(g.vwgt, dtype=np.int64)[:g.n]
+
+
+def assert_same_graph(got, exp):
+    gx, ga, gw, gv = canon(got)
+    ex, ea, ew, ev = canon(exp)
+    assert got.n == exp.n
+    assert np.array_equal(gv, ev), "node weights differ"
+    assert np.array_equal(gx, ex), "row offsets differ"
+    assert np.array_equal(ga, ea), "neighbours differ"
+    assert np.array_equal(gw, ew), "edge weights differ"
+
+
+def _level_fields(st):
+    return (st.lp_subrounds, st.lp_moves, st.clusters_lp, st.clusters_2hop, st.clusters_final, st.n_next)
+
+
+# --------------------------------------------------------------- coarsening
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("seed", [1, 7])
+def test_coarsen_matches_oracle(gp, ctx, name, seed):
+    g = GRAPHS[name]
+    W = int(g.vwgt.sum())
+    for U in (max(1, W // (160 * 2)), 6):
+        dg = gp.DeviceGraph.from_host(g)
+        cmap, nc, st, label = ctx.gp_coarsen(dg, U, 1, seed, want_label=True)
+        olabel, oncl, ost = orc.cluster(g, U, 1, seed)
+        ocmap, onc, _ = orc.coarsen(g, U, 1, seed)
+        assert np.array_equal(label.cpu().numpy(), olabel), f"labels differ ({name}, U={U})"
+        assert nc == onc
+        assert np.array_equal(cmap.cpu().numpy(), ocmap)
+        assert (st.lp_subrounds, st.lp_moves, st.clusters_lp, st.clusters_2hop, st.clusters_final) == \
+            (ost.lp_subrounds, ost.lp_moves, ost.clusters_lp, ost.clusters_2hop, ost.clusters_final)
+
+
+@pytest.mark.parametrize("subs", [0, 1, 2, 3, 7, 9, 17])
+def test_lp_state_after_each_subround(gp, ctx, subs):
+    g = GRAPHS["er_w"]
+    cfg_g = gp.default_config(dbg_max_subrounds=subs, two_hop=0, isolated=0)
+    cfg_o = orc.Config.default(dbg_max_subrounds=subs, two_hop=0, isolated=0)
+    dg = gp.DeviceGraph.from_host(g)
+    for U in (5, 40):
+        _, nc, st, label = ctx.gp_coarsen(dg, U, 2, 3, cfg_g, want_label=True)
+        olabel, oncl, ost = orc.cluster(g, U, 2, 3, cfg_o)
+        assert np.array_equal(label.cpu().numpy(), olabel)
+        assert nc == oncl and st.lp_subrounds == ost.lp_subrounds
+
+
+def test_coarsen_config_variants(gp, ctx):
+    g = GRAPHS["iso"]
+    for kw in ({"two_hop": 0}, {"isolated": 0}, {"lp_subrounds": 1}, {"lp_subrounds": 3, "lp_rounds": 2},
+               {"shrink_num": 1000, "shrink_den": 1}, {"lp_rounds": 0}):
+        dg = gp.DeviceGraph.from_host(g)
+        cmap, nc, st = ctx.gp_coarsen(dg, 9, 4, 11, gp.default_config(**kw))
+        ocmap, onc, _ = orc.coarsen(g, 9, 4, 11, orc.Config.default(**kw))
+        assert nc == onc and np.array_equal(cmap.cpu().numpy(), ocmap), kw
+
+
+def test_coarsen_tiny_and_degenerate(gp, ctx):
+    cases = [hand(1, []), hand(2, [(0, 1)]), hand(3, []), hand(5, clique(5)), star(1),
+             hand(4, [(0, 1), (2, 3)], weights=[5, 1], vwgt=[3, 1, 2, 2])]
+    for g in cases:
+        for U in (1, 2, 100):
+            dg = gp.DeviceGraph.from_host(g)
+            cmap, nc, st = ctx.gp_coarsen(dg, U, 1, 1)
+            ocmap, onc, _ = orc.coarsen(g, U, 1, 1)
+            assert nc == onc and np.array_equal(cmap.cpu().numpy(), ocmap)
+
+
+# -------------------------------------------------------------- contraction
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_contract_matches_oracle(gp, ctx, name):
+    g = GRAPHS[name]
+    ocmap, onc, _ = orc.coarsen(g, 8, 1, 1)
+    rng = np.random.default_rng(5)
+    rcmap = rng.integers(0, max(1, g.n // 3), g.n).astype(np.int32)
+    used = np.unique(rcmap)
+    rcmap = np.searchsorted(used, rcmap).astype(np.int32)
+    cmaps = [(ocmap, onc), (rcmap, len(used)), (np.zeros(g.n, np.int32), 1)]
+    import torch
+    for cmap, nc in cmaps:
+        dg = gp.DeviceGraph.from_host(g)
+        out = ctx.gp_contract(dg, torch.from_numpy(cmap).cuda(), nc)
+        got = out.to_host()
+        exp = orc.contract(g, cmap, nc)
+        assert_same_graph(got, exp)
+        out.release()
+
+
+# ----------------------------------------------------------- sparsification
+
+@pytest.mark.parametrize("wmax", [1, 5, 100000])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_sparsify_matches_oracle(gp, ctx, wmax, mode):
+    g = gg.with_edge_weights(gg.er(4000, 50000, 6), wmax)
+    dg = gp.DeviceGraph.from_host(g)
+    m = g.m
+    for mh in (0, 1, 3, m // 7, m // 2, m - 1, m, 2 * m):
+        out, st = ctx.gp_sparsify(dg, mh, 3, 9, mode)
+        exp, ost = orc.sparsify(g, mh, 3, 9, mode)
+        assert_same_graph(out.to_host(), exp)
+        assert (st.omega_t, st.n_greater, st.n_equal, st.threshold) == \
+            (ost.omega_t, ost.n_greater, ost.n_equal, ost.threshold)
+        out.release()
+
+
+def test_sparsify_heavy_hub_rows(gp, ctx):
+    g = gg.with_edge_weights(gg.rmat(13, 16, seed=2), 9)
+    dg = gp.DeviceGraph.from_host(g)
+    for mh in (g.m // 5, g.m // 2):
+        out, st = ctx.gp_sparsify(dg, mh, 2, 4, 1)
+        exp, ost = orc.sparsify(g, mh, 2, 4, 1)
+        assert_same_graph(out.to_host(), exp)
+        out.release()
+
+
+# ---------------------------------------------- initial partition, balance
+
+def _coarse(g, levels=2, k=4):
+    cur = g
+    W = int(g.vwgt.sum())
+    U = orc.cluster_bound(W, k)
+    for i in range(levels):
+        cmap, nc, _ = orc.coarsen(cur, U, i + 1, 1)
+        cur = orc.contract(cur, cmap, nc)
+    return cur
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 8, 16])
+def test_initial_partition_matches_oracle(gp, ctx, k):
+    for g in (_coarse(GRAPHS["er_w"]), _coarse(GRAPHS["grid"]), GRAPHS["star"], _coarse(GRAPHS["rmat12"])):
+        dg = gp.DeviceGraph.from_host(g)
+        blk = ctx.gp_initial_partition(dg, k, 0.03, 5)
+        oblk = orc.initial_partition(g, k, 30000, 5)
+        assert np.array_equal(blk.cpu().numpy(), oblk)
+
+
+def test_initial_partition_large_subproblem_uses_global_state(gp, ctx):
+    g = gg.er(14000, 40000, 8)   # above the shared-memory node limit
+    dg = gp.DeviceGraph.from_host(g)
+    blk = ctx.gp_initial_partition(dg, 2, 0.03, 2, gp.default_config(ip_trials=2))
+    oblk = orc.initial_partition(g, 2, 30000, 2, trials=2)
+    assert np.array_equal(blk.cpu().numpy(), oblk)
+
+
+@pytest.mark.parametrize("k", [2, 5, 8])
+def test_rebalance_matches_oracle(gp, ctx, k):
+    import torch
+    g = gg.with_node_weights(gg.grid2d(40, 40), 4)
+    W = int(g.vwgt.sum())
+    Lmax = orc.lmax(W, k, 30000)
+    rng = np.random.default_rng(k)
+    blk = np.where(rng.random(g.n) < 0.6, 0, rng.integers(0, k, g.n)).astype(np.int32)
+    dg = gp.DeviceGraph.from_host(g)
+    t = torch.from_numpy(blk.copy()).cuda()
+    mv = ctx.gp_rebalance(dg, k, Lmax, t)
+    oblk, omv = orc.rebalance(g, k, Lmax, blk)
+    assert mv == omv
+    assert np.array_equal(t.cpu().numpy(), oblk)
+
+
+@pytest.mark.parametrize("k", [2, 4, 16, 64])
+def test_refine_matches_oracle(gp, ctx, k):
+    import torch
+    for g in (GRAPHS["er_w"], GRAPHS["rmat12"], GRAPHS["grid"]):
+        W = int(g.vwgt.sum())
+        Lmax = orc.lmax(W, k, 30000)
+        rng = np.random.default_rng(k)
+        blk = rng.integers(0, k, g.n).astype(np.int32)
+        blk, _ = orc.rebalance(g, k, Lmax, blk)
+        dg = gp.DeviceGraph.from_host(g)
+        t = torch.from_numpy(blk.copy()).cuda()
+        mv = ctx.gp_refine(dg, k, Lmax, 2, 13, t)
+        oblk, omv = orc.refine(g, k, Lmax, 2, 13, blk)
+        assert mv == omv
+        assert np.array_equal(t.cpu().numpy(), oblk)
+
+
+def test_cut_and_project(gp, ctx):
+    import torch
+    g = GRAPHS["er_w"]
+    k = 7
+    blk = np.random.default_rng(1).integers(0, k, g.n).astype(np.int32)
+    dg = gp.DeviceGraph.from_host(g)
+    cut, bw = ctx.gp_cut(dg, torch.from_numpy(blk).cuda(), k)
+    assert cut == orc.cut(g, blk)
+    assert np.array_equal(bw, np.bincount(blk, weights=g.vwgt, minlength=k).astype(np.int64))
+    cmap = np.random.default_rng(2).integers(0, 100, g.n).astype(np.int32)
+    coarse = np.random.default_rng(3).integers(0, k, 100).astype(np.int32)
+    fine = ctx.gp_project(torch.from_numpy(cmap).cuda(), torch.from_numpy(coarse).cuda(), g.n)
+    assert np.array_equal(fine.cpu().numpy(), coarse[cmap])
+
+
+# ---------------------------------------------------------------- partition
+
+def _check_partition(gp, ctx, g, k, eps, seed, cfg_kw=None):
+    cfg_kw = cfg_kw or {}
+    dg = gp.DeviceGraph.from_host(g)
+    blocks, cut, st = ctx.gp_partition(dg, k, eps, seed, gp.default_config(**cfg_kw))
+    r = orc.partition(g, k, eps, seed, orc.Config.default(**cfg_kw))
+    assert r.rc == orc.OK
+    assert cut == r.cut
+    assert np.array_equal(blocks.cpu().numpy(), r.blocks)
+    assert st.levels == r.stats.levels
+    for a, b in zip([st.lv[i] for i in range(st.levels)], [r.stats.lv[i] for i in range(r.stats.levels)]):
+        for f in ("n", "n_next", "m", "m_coarse", "m_hat", "m_next", "triggered", "omega_t",
+                  "n_greater", "n_equal", "threshold", "lp_subrounds", "lp_moves", "clusters_lp",
+                  "clusters_2hop", "clusters_final"):
+            assert getattr(a, f) == getattr(b, f), f
+    assert (st.U, st.Lmax, st.W, st.ip_cut, st.rebalance_moves, st.n_coarsest) == \
+        (r.stats.U, r.stats.Lmax, r.stats.W, r.stats.ip_cut, r.stats.rebalance_moves, r.stats.n_coarsest)
+    assert np.bincount(r.blocks, weights=g.vwgt, minlength=k).max() <= st.Lmax
+    return st
+
+
+def test_partition_er_c1_matches_oracle(gp, ctx):
+    g = gg.er(65536, 524288, 1)
+    st = _check_partition(gp, ctx, g, 2, 0.03, 1)
+    assert any(st.lv[i].triggered for i in range(st.levels))
+
+
+@pytest.mark.parametrize("name,k", [("er", 4), ("er_w", 8), ("rmat12", 16), ("grid", 3), ("iso", 5),
+                                    ("star", 2), ("dense", 6), ("matching", 4)])
+def test_partition_matches_oracle(gp, ctx, name, k):
+    _check_partition(gp, ctx, GRAPHS[name], k, 0.03, 2)
+
+
+@pytest.mark.parametrize("kw", [{"sparsifier": 0}, {"sparsifier": 2}, {"ref_rounds": 0},
+                                {"coarsest_factor": 20}, {"ip_trials": 1}])
+def test_partition_config_variants(gp, ctx, kw):
+    _check_partition(gp, ctx, gg.er(20000, 100000, 3), 4, 0.05, 4, kw)
+
+
+def test_partition_rmat_scale15(gp, ctx):
+    _check_partition(gp, ctx, gg.rmat(15, 16, seed=1), 64, 0.03, 1)
+
+
+def test_partition_host_entry_matches_device(gp, ctx):
+    g = GRAPHS["er_w"]
+    dg = gp.DeviceGraph.from_host(g)
+    blocks, cut, st = ctx.gp_partition(dg, 4, 0.03, 3)
+    hb, hcut, hst = ctx.gp_partition_host(g.n, g.m2, g.xadj.astype(np.int32), g.adjncy, g.vwgt, g.adjwgt,
+                                          4, 0.03, 3)
+    assert hcut == cut
+    assert np.array_equal(hb[:g.n], blocks.cpu().numpy())
+
+
+def test_partition_trivial_cases(gp, ctx):
+    g = GRAPHS["er"]
+    dg = gp.DeviceGraph.from_host(g)
+    blocks, cut, _ = ctx.gp_partition(dg, 1, 0.03, 1)
+    assert cut == 0 and (blocks.cpu().numpy() == 0).all()
+    two_k5 = hand(10, clique(5) + clique(5, 5) + [(4, 5)])
+    b, c, _ = ctx.gp_partition(gp.DeviceGraph.from_host(two_k5), 2, 0.03, 1)
+    assert c == 1
+    e = hand(1, [])
+    b, c, _ = ctx.gp_partition(gp.DeviceGraph.from_host(e), 3, 0.03, 1)
+    assert c == 0
+
+
+def test_validation_errors(gp, ctx):
+    g = hand(4, [(0, 1), (1, 2), (2, 3)])
+    bad_w = gg.Graph(g.n, g.xadj.copy(), g.adjncy.copy(), g.vwgt.copy(), g.adjwgt.copy())
+    bad_w.adjwgt[0] = 5
+    loop = gg.Graph(g.n, g.xadj.copy(), g.adjncy.copy(), g.vwgt.copy(), g.adjwgt.copy())
+    loop.adjncy[0] = 0
+    zero = gg.Graph(g.n, g.xadj.copy(), g.adjncy.copy(), g.vwgt.copy(), g.adjwgt.copy())
+    zero.vwgt[1] = 0
+    heavy = gg.Graph(g.n, g.xadj.copy(), g.adjncy.copy(), np.array([1, 1, 1, 9], np.int32), g.adjwgt.copy())
+    big = gg.Graph(g.n, g.xadj.copy(), g.adjncy.copy(), g.vwgt.copy(), np.full(g.m2, 2**30, np.int32))
+    for bad, status in ((bad_w, gp.GP_ERR_INVALID), (loop, gp.GP_ERR_INVALID), (zero, gp.GP_ERR_INVALID),
+                        (heavy, gp.GP_ERR_INFEASIBLE), (big, gp.GP_ERR_OVERFLOW)):
+        with pytest.raises(gp.GpError) as ei:
+            ctx.gp_partition(gp.DeviceGraph.from_host(bad), 2, 0.03, 1)
+        assert ei.value.status == status
+    with pytest.raises(gp.GpError):
+        ctx.gp_partition(gp.DeviceGraph.from_host(g), 0, 0.03, 1)
+    with pytest.raises(gp.GpError):
+        ctx.gp_partition(gp.DeviceGraph.from_host(g), 2, 0.0, 1)
+    # the context stays usable after errors
+    blocks, cut, _ = ctx.gp_partition(gp.DeviceGraph.from_host(g), 2, 0.03, 1)
+    assert cut == orc.partition(g, 2, 0.03, 1).cut
