@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: coarsening throughput of the GB300 partitioner on the 2^26-node
+Erdos-Renyi graph (671,088,640 undirected edges, unit weights, k = 128,
+eps = 0.03, seed 1), printed as one JSON line.
+
+A step is one full gp_partition call (validation, coarsening with
+sparsification, initial partitioning, uncoarsening with refinement) on the
+device-resident graph.  `value` is coarsening edges/s: input edges divided
+by the device time of the coarsening phase (CUDA events on the library's
+stream inside each step), summed over the timed steps.  `e2e` is the same
+graph through gp_partition_host from pinned host memory: input copies,
+partition and the copy of the block ids back are all in its timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (launched by torchrun) every rank partitions its own replica of
+the graph (the method does not shard one graph); value sums all ranks' edges
+over the slowest rank's time.  `--impl reference` times the CPU oracle of
+the same method (single-threaded C) on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("coarsening edges/s and HBM GB/s (% of GB300 peak); batched graphs/s, served p50/p99 ms")
+WORKLOAD = dict(name="erdos_renyi_n2^26_m671088640_k128", n=1 << 26, m=671_088_640, k=128, eps=0.03,
+                seed=1)
+SMALL = dict(name="erdos_renyi_n2^20_m10485760_k128", n=1 << 20, m=10_485_760, k=128, eps=0.03, seed=1)
+# bounded CPU sample of the same workload family (same degree, same k)
+CPU_SAMPLE = dict(name="erdos_renyi_n2^21_m20971520_k128", n=1 << 21, m=20_971_520, k=128, seed=1)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu_index), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------- inputs
+
+def make_graph(w, rank: int, world: int):
+    """Rank 0 draws the graph; other ranks read it from a shared file."""
+    import numpy as np
+    import graphgen as gg
+    if world == 1:
+        t = time.time()
+        g = gg.er(w["n"], w["m"], w["seed"])
+        log(f"[bench] generated {w['name']} in {time.time() - t:.1f}s")
+        return g
+    import torch.distributed as dist
+    shared = os.path.join(tempfile.gettempdir(), f"gpbench_{w['name']}_{os.environ.get('MASTER_PORT', '0')}")
+    if rank == 0:
+        g = gg.er(w["n"], w["m"], w["seed"])
+        os.makedirs(shared, exist_ok=True)
+        np.save(os.path.join(shared, "xadj.npy"), g.xadj)
+        np.save(os.path.join(shared, "adjncy.npy"), g.adjncy)
+    dist.barrier()
+    if rank != 0:
+        xadj = np.load(os.path.join(shared, "xadj.npy"), mmap_mode="r")
+        adj = np.load(os.path.join(shared, "adjncy.npy"), mmap_mode="r")
+        g = gg.Graph(w["n"], np.asarray(xadj), np.asarray(adj), np.ones(w["n"], np.int32),
+                     np.ones(len(adj), np.int32), w["name"])
+    dist.barrier()
+    if rank == 0:
+        for f in ("xadj.npy", "adjncy.npy"):
+            os.unlink(os.path.join(shared, f))
+        os.rmdir(shared)
+    return g
+
+
+# ---------------------------------------------------------------- CPU arm
+
+def cpu_sample_run(steps: int = 1):
+    """Times the oracle's coarsening phase on the bounded CPU sample."""
+    import graphgen as gg
+    import oracle as orc
+    g = gg.er(CPU_SAMPLE["n"], CPU_SAMPLE["m"], CPU_SAMPLE["seed"])
+    times = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        orc.coarsen_only(g, CPU_SAMPLE["k"], CPU_SAMPLE["seed"])
+        times.append(time.perf_counter() - t)
+    return g.m, times
+
+
+def cpu_baseline_obj(m, times):
+    return {"value": m / statistics.mean(times), "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": (f"coarsening phase (Alg. 1) of the single-threaded C oracle on "
+                       f"{CPU_SAMPLE['name']} (same degree and k as the workload), "
+                       f"{len(times)} run(s), {statistics.mean(times):.2f} s each, host cpu "
+                       f"{os.cpu_count()} cores available, 1 used")}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_sample_run(1)
+    m, times = cpu_sample_run(args.steps)
+    cb = cpu_baseline_obj(m, times)
+    w = SMALL if args.small else WORKLOAD
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w["name"], "k": w["k"], "eps": w["eps"], "seed": w["seed"],
+                       "sample": CPU_SAMPLE["name"], "parallelism": "replicas"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2504_17615_gb300 as gp
+    from paper_2504_17615_gb300 import build as gpbuild
+
+    w = SMALL if args.small else WORKLOAD
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gpbuild.build()
+    g = make_graph(w, rank, world)
+    n, m2 = g.n, g.m2
+    ctx = gp.Context(local)
+    stream = ctx.stream
+    t0 = time.time()
+    dg = gp.DeviceGraph.from_host(g)
+    torch.cuda.synchronize()
+    log(f"[bench] rank {rank}: uploaded n={n} m={g.m} in {time.time() - t0:.1f}s")
+    blocks = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def step():
+        return ctx.gp_partition(dg, w["k"], w["eps"], w["seed"], blocks=blocks)
+
+    for i in range(args.warmup):
+        _, cut, st = step()
+        log(f"[bench] warmup {i}: {st.ms_total:.1f} ms (coarsen {st.ms_coarsen:.1f}) cut={cut} "
+            f"levels={st.levels}")
+    ctx.profile_reset()
+    ctx.profile(True)
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if cvd and cvd.split(",")[local].strip().isdigit():
+        gpu_index = int(cvd.split(",")[local])
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = gp.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        _, cut, st = step()
+        stats.append((st.ms_coarsen, st.ms_initial, st.ms_uncoarsen, st.ms_total, cut, st.levels))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = gp.launch_count() - launches0
+    clk = clocks.stop()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    step_ms = ev0.elapsed_time(ev1)
+    coarsen_ms = sum(s[0] for s in stats)
+    if world > 1:
+        t = torch.tensor([step_ms, coarsen_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, coarsen_ms = float(t[0]), float(t[1])
+    value = world * g.m * args.steps / (coarsen_ms / 1000.0)
+
+    # roofline of the dominant kernel class (by device time in the timed region)
+    peak, peak_kind = measured_peaks()
+    dom = max((k for k in prof if prof[k]["bytes"] > 0), key=lambda k: prof[k]["ms"])
+    dom_ms = prof[dom]["ms"]
+    achieved = prof[dom]["bytes"] / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback", "traffic": args.traffic,
+            "launches": prof[dom]["launches"], "ms": dom_ms,
+            "algorithmic_bytes": prof[dom]["bytes"]}
+
+    # end to end through the host entry point from pinned memory
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(np.ascontiguousarray(g.xadj, dtype=np.int32)).pin_memory()
+        ha = torch.from_numpy(g.adjncy).pin_memory()
+        hv = torch.from_numpy(np.ascontiguousarray(g.vwgt)).pin_memory()
+        hw = torch.from_numpy(np.ascontiguousarray(g.adjwgt)).pin_memory()
+        hb = torch.empty(n, dtype=torch.int32).pin_memory()
+        ctx.gp_partition_host(n, m2, hx, ha, hv, hw, w["k"], w["eps"], w["seed"], blocks=hb)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.gp_partition_host(n, m2, hx, ha, hv, hw, w["k"], w["eps"], w["seed"], blocks=hb)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t
+        if world > 1:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt[0])
+        e2e = {"value": world * g.m * args.steps / e2e_s, "unit": "edges/s",
+               "what": "gp_partition_host: H2D of the CSR, full partition, D2H of the block ids",
+               "ms_per_step": 1000 * e2e_s / args.steps,
+               "h2d_bytes_per_step": 4 * ((n + 1) + 2 * m2 + n), "d2h_bytes_per_step": 4 * n}
+
+    if rank != 0:
+        return 0
+    cb = None
+    if not args.no_cpu_baseline:
+        m_s, times = cpu_sample_run(1)
+        cb = cpu_baseline_obj(m_s, times)
+    mean = lambda i: statistics.mean(s[i] for s in stats)
+    line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "n": w["n"], "m": w["m"], "k": w["k"], "eps": w["eps"],
+                       "seed": w["seed"], "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs (CSR 10.7 GB) larger than L2, no flush",
+                       "value_is": "input edges / coarsening-phase device time"},
+            "partition_edges_per_s": world * g.m * args.steps / (step_ms / 1000.0),
+            "phases_ms": {"coarsen": mean(0), "initial": mean(1), "uncoarsen": mean(2), "total": mean(3)},
+            "cut": stats[-1][4], "levels": stats[-1][5],
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches // max(args.steps, 1),
+            "gpu_launches_total": launches, "clocks": clk,
+            "kernel_classes": {k: v for k, v in prof.items() if v["launches"]}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--small", action="store_true", help="2^20-node graph (quick checks)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if measured")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("[bench] warning: fewer than 3 warm-up steps")
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -126,6 +126,8 @@ void gp_destroy(gp_ctx *ctx);
 const char *gp_last_error(const gp_ctx *ctx);
 /* Library build string (version, compute capability compiled for). */
 const char *gp_version(void);
+/* Number of kernels this library has launched in this process (all contexts). */
+int64_t gp_launch_count(void);
 
 /*
  * One coarsening clustering of G_level (Sec. 3, Sec. 4.1): size-constrained

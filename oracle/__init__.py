@@ -116,6 +116,7 @@ def _load():
                 "or_refine": (ctypes.c_int, G + [i32, i64, i32, u64, P, P, P]),
                 "or_cut": (i64, [i32, P, P, P, P]),
                 "or_partition": (ctypes.c_int, G + [i32, i64, u64, P, P, P, P]),
+                "or_coarsen_only": (ctypes.c_int, G + [i32, u64, P, P]),
                 "or_free": (None, [P]),
             }
             for name, (res, args) in sig.items():
@@ -298,6 +299,17 @@ class Result:
 
     def levels(self) -> list[dict]:
         return [self.stats.lv[i].as_dict() for i in range(self.stats.levels)]
+
+
+def coarsen_only(g, k: int, seed: int, cfg: Config | None = None) -> Stats:
+    """Runs only the coarsening phase (Alg. 1) and returns its per-level records."""
+    cfg = cfg or Config.default()
+    keep, a = _args(g)
+    st = Stats()
+    rc = _load().or_coarsen_only(*a, k, seed, ctypes.byref(cfg), ctypes.byref(st))
+    if rc != OK:
+        raise RuntimeError(f"or_coarsen_only failed: {rc}")
+    return st
 
 
 def partition(g, k: int, eps: float, seed: int, cfg: Config | None = None) -> Result:

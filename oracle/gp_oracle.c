@@ -797,35 +797,11 @@ int or_trigger(int64_t m_coarse, int64_t m_hat, const or_config *cfg) {
 /* ------------------------------------------------------- full partitioner */
 
 /*
- * Multilevel partitioning (Sec. 2, Alg. 1, Sec. 4.3): coarsen until
- * n <= coarsest_factor * k or the shrink is too small (R13: n' * 21 > n * 20),
- * sparsifying each coarse graph that exceeds rho * m_hat; recursive
- * bisection of the coarsest graph plus R19; then project and refine level
- * by level.  Hash levels: coarsening G_i uses level i (G_1 = input), the
- * sparsifier producing G_{i+1} uses level i+1, refining G_i uses level i.
+ * The coarsening loop of Alg. 1: G[0] is the input; fills G[1..L] and the
+ * coarse-id maps C[0..L-1] (owned: free with free / og_free); returns L.
  */
-int or_partition(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
-                 const int32_t *adjwgt, int32_t k, int64_t eps_ppm, uint64_t seed,
-                 const or_config *cfg, int32_t *blocks, int64_t *cut_out, or_stats *st) {
-  if (k < 1 || eps_ppm < 1) return OR_INVALID;
-  int64_t W = 0;
-  int rc = or_validate(n, xadj, adjncy, vwgt, adjwgt, &W);
-  if (rc != OR_OK) return rc;
-  int64_t Lmax = or_lmax(W, k, eps_ppm);
-  for (int32_t v = 0; v < n; v++)
-    if (vwgt[v] > Lmax) return OR_INFEASIBLE;
-  if (st) { memset(st, 0, sizeof *st); st->W = W; st->Lmax = Lmax; }
-  if (k == 1 || n == 0) {
-    for (int32_t v = 0; v < n; v++) blocks[v] = 0;
-    if (cut_out) *cut_out = 0;
-    if (st) st->n_coarsest = n;
-    return OR_OK;
-  }
-  int64_t U = or_cluster_bound(W, k, cfg->cluster_factor);
-  if (st) st->U = U;
-  og G[OR_MAX_LEVELS + 1];
-  int32_t *C[OR_MAX_LEVELS + 1];
-  G[0] = view(n, xadj, adjncy, vwgt, adjwgt);
+static int32_t coarsen_hierarchy(og *G, int32_t **C, int32_t k, int64_t U, uint64_t seed,
+                                 const or_config *cfg, or_stats *st) {
   int32_t L = 0;
   int32_t maxl = cfg->max_levels < OR_MAX_LEVELS ? cfg->max_levels : OR_MAX_LEVELS;
   while ((int64_t)G[L].n > (int64_t)cfg->coarsest_factor * k && L < maxl) {
@@ -867,6 +843,40 @@ int or_partition(int32_t n, const int64_t *xadj, const int32_t *adjncy, const in
     G[L + 1] = Gc;
     L++;
   }
+  return L;
+}
+
+/*
+ * Multilevel partitioning (Sec. 2, Alg. 1, Sec. 4.3): coarsen until
+ * n <= coarsest_factor * k or the shrink is too small (R13: n' * 21 > n * 20),
+ * sparsifying each coarse graph that exceeds rho * m_hat; recursive
+ * bisection of the coarsest graph plus R19; then project and refine level
+ * by level.  Hash levels: coarsening G_i uses level i (G_1 = input), the
+ * sparsifier producing G_{i+1} uses level i+1, refining G_i uses level i.
+ */
+int or_partition(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                 const int32_t *adjwgt, int32_t k, int64_t eps_ppm, uint64_t seed,
+                 const or_config *cfg, int32_t *blocks, int64_t *cut_out, or_stats *st) {
+  if (k < 1 || eps_ppm < 1) return OR_INVALID;
+  int64_t W = 0;
+  int rc = or_validate(n, xadj, adjncy, vwgt, adjwgt, &W);
+  if (rc != OR_OK) return rc;
+  int64_t Lmax = or_lmax(W, k, eps_ppm);
+  for (int32_t v = 0; v < n; v++)
+    if (vwgt[v] > Lmax) return OR_INFEASIBLE;
+  if (st) { memset(st, 0, sizeof *st); st->W = W; st->Lmax = Lmax; }
+  if (k == 1 || n == 0) {
+    for (int32_t v = 0; v < n; v++) blocks[v] = 0;
+    if (cut_out) *cut_out = 0;
+    if (st) st->n_coarsest = n;
+    return OR_OK;
+  }
+  int64_t U = or_cluster_bound(W, k, cfg->cluster_factor);
+  if (st) st->U = U;
+  og G[OR_MAX_LEVELS + 1];
+  int32_t *C[OR_MAX_LEVELS + 1];
+  G[0] = view(n, xadj, adjncy, vwgt, adjwgt);
+  int32_t L = coarsen_hierarchy(G, C, k, U, seed, cfg, st);
   if (st) { st->levels = L; st->n_coarsest = G[L].n; }
   /* initial partition of the coarsest graph */
   og *gc = &G[L];
@@ -890,6 +900,29 @@ int or_partition(int32_t n, const int64_t *xadj, const int32_t *adjncy, const in
   int64_t cut = or_cut(n, xadj, adjncy, adjwgt, blocks);
   if (cut_out) *cut_out = cut;
   if (st) st->cut = cut;
+  for (int32_t i = 0; i < L; i++) { free(C[i]); og_free(&G[i + 1]); }
+  return OR_OK;
+}
+
+/*
+ * The coarsening phase alone (Alg. 1 with the clustering of Sec. 4.1 and the
+ * sparsifier of Sec. 4.2) on a validated graph; fills the per-level records
+ * of st and frees the hierarchy.  Used to time the method's coarsening.
+ */
+int or_coarsen_only(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                    const int32_t *adjwgt, int32_t k, uint64_t seed, const or_config *cfg,
+                    or_stats *st) {
+  if (k < 1) return OR_INVALID;
+  int64_t W = 0;
+  for (int32_t v = 0; v < n; v++) W += vwgt[v];
+  if (st) { memset(st, 0, sizeof *st); st->W = W; }
+  int64_t U = or_cluster_bound(W, k, cfg->cluster_factor);
+  if (st) st->U = U;
+  og G[OR_MAX_LEVELS + 1];
+  int32_t *C[OR_MAX_LEVELS + 1];
+  G[0] = view(n, xadj, adjncy, vwgt, adjwgt);
+  int32_t L = coarsen_hierarchy(G, C, k, U, seed, cfg, st);
+  if (st) { st->levels = L; st->n_coarsest = G[L].n; }
   for (int32_t i = 0; i < L; i++) { free(C[i]); og_free(&G[i + 1]); }
   return OR_OK;
 }

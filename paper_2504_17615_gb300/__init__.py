@@ -105,6 +105,7 @@ def _load():
         sig = {
             "gp_config_default": (None, [C]),
             "gp_version": (ctypes.c_char_p, []),
+            "gp_launch_count": (i64, []),
             "gp_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P, ctypes.POINTER(gp_allocator)]),
             "gp_destroy": (None, [P]),
             "gp_last_error": (ctypes.c_char_p, [P]),
@@ -424,3 +425,8 @@ class Context:
 
 def version() -> str:
     return _load().gp_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(_load().gp_launch_count())

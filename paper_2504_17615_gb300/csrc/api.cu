@@ -73,6 +73,8 @@ void gp_config_default(gp_config *c) {
 
 const char *gp_version(void) { return "gp-gb300 1.0 (sm_103a)"; }
 
+int64_t gp_launch_count(void) { return gp::g_launch_count.load(); }
+
 gp_status gp_create(gp_ctx **out, int device, void *stream, const gp_allocator *alloc) {
   if (!out) return GP_ERR_INVALID;
   *out = nullptr;

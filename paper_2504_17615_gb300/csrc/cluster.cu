@@ -151,6 +151,7 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
       cmax.zero();
       const int gc = grid_for(count, 256, ctx->num_sms * 8);
       k_fav_cmax<<<gc, 256, 0, ctx->stream>>>(keys.get(), count, g.vwgt, cmax.get());
+      GP_LAUNCH_CHECK();
       k_fav_flags<<<gc, 256, 0, ctx->stream>>>(keys.get(), count, cmax.get(), U, merge.get(),
                                                leader.get());
       GP_LAUNCH_CHECK();
@@ -180,6 +181,7 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
       const int64_t gsz = U / cm;
       DBuf<int32_t> list(ctx, (size_t)niso);
       k_iso_list<<<grid, 256, 0, ctx->stream>>>(flag.get(), rank.get(), n, list.get());
+      GP_LAUNCH_CHECK();
       const int64_t M = ncl - n_min;
       k_iso_apply<<<grid, 256, 0, ctx->stream>>>(flag.get(), rank.get(), list.get(), n, gsz, M, label);
       GP_LAUNCH_CHECK();

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -32,7 +33,14 @@ struct Error {
                                   " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
   } while (0)
 
-#define GP_LAUNCH_CHECK() GP_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by GP_LAUNCH_CHECK(), which
+// also counts it (gp_launch_count).
+extern std::atomic<long long> g_launch_count;
+#define GP_LAUNCH_CHECK()                                           \
+  do {                                                              \
+    ::gp::g_launch_count.fetch_add(1, std::memory_order_relaxed);   \
+    GP_CUDA(cudaGetLastError());                                    \
+  } while (0)
 
 #define GP_REQUIRE(cond, st, msg) \
   do {                            \

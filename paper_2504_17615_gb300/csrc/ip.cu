@@ -251,6 +251,7 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
     GP_CUDA(cudaMemcpyAsync(start.get(), hs.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice,
                             ctx->stream));
     k_sub_fill<<<grid, 256, 0, ctx->stream>>>(sp.get(), n, start.get(), cursor.get(), list.get(), loc.get());
+    GP_LAUNCH_CHECK();
     k_dp<<<grid_for((int64_t)n * 32, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(
         g.xadj, g.adjncy, g.adjwgt, sp.get(), n, dp.get());
     GP_LAUNCH_CHECK();
@@ -399,6 +400,7 @@ int64_t rebalance_blocks(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t Lmax
   bw.zero();
   moves.zero();
   k_block_weights<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(blocks, g.vwgt, g.n, bw.get());
+  GP_LAUNCH_CHECK();
   k_rebalance<<<1, kRbThreads, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, g.vwgt, g.n, k, Lmax, blocks,
                                                  reinterpret_cast<int64_t *>(bw.get()), moves.get());
   GP_LAUNCH_CHECK();

@@ -665,6 +665,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       {
         ProfScope ps(ctx, p.prof_accept);
         k_reset_nov<<<1, 1, 0, ctx->stream>>>(C);
+        GP_LAUNCH_CHECK();
         k_decide<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(),
                                                       g.vwgt, weight, incoming.get(), p.bound,
                                                       acc.get(), ov_key.get(), ov_val.get(), C, kprio);
@@ -681,8 +682,10 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         radix_sort_pairs(ctx, ov_key.get(), ov_val.get(), nov, kbits);
         const int gsmall = grid_for(nov, 256, grid);
         k_fix_runs<<<gsmall, 256, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov);
+        GP_LAUNCH_CHECK();
         DBuf<int64_t> cs(ctx, (size_t)nov);
         k_ov_weights<<<gsmall, 256, 0, ctx->stream>>>(ov_val.get(), nov, g.vwgt, cs.get());
+        GP_LAUNCH_CHECK();
         scan_exclusive_i64(ctx, cs.get(), cs.get(), nov, nullptr);
         k_ov_accept<<<gsmall, 256, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov, cs.get(), g.vwgt,
                                                      weight, p.bound, acc.get());
@@ -739,6 +742,7 @@ void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, c
   k_bucket_count<<<grid_for(n, kThreads, grid), kThreads, 0, ctx->stream>>>(b, nkeys, cnt.get());
   GP_LAUNCH_CHECK();
   k_bucket_offsets<<<1, 1, 0, ctx->stream>>>(cnt.get(), nkeys, offs.get(), cursor.get(), nullptr);
+  GP_LAUNCH_CHECK();
   k_bucket_scatter<<<grid_for(n, kChunk, grid), kThreads, 0, ctx->stream>>>(b, nkeys, cursor.get(),
                                                                            list.get());
   GP_LAUNCH_CHECK();
@@ -748,6 +752,7 @@ void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, c
   keys.reset(ctx, (size_t)(total > 0 ? total : 1));
   if (total == 0) return;
   k_fill_u64<<<grid_for(total, 256, grid), 256, 0, ctx->stream>>>(keys.get(), total, ~0ull);
+  GP_LAUNCH_CHECK();
   RateTables tables;
   make_tables(ctx, g, tables);
   RateArgs a{};

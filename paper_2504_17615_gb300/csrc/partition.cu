@@ -158,10 +158,11 @@ void block_weights_dev(gp_ctx *ctx, const DevGraph &g, const int32_t *blocks, in
   if (k <= 4096) {
     k_bweights<<<grid_for(g.n, 256, ctx->num_sms * 4), 256, sizeof(unsigned long long) * k, ctx->stream>>>(
         blocks, g.vwgt, g.n, k, bw);
+    GP_LAUNCH_CHECK();
   } else {
     k_bweights_global<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(blocks, g.vwgt, g.n, bw);
+    GP_LAUNCH_CHECK();
   }
-  GP_LAUNCH_CHECK();
 }
 
 }  // namespace

@@ -4,6 +4,8 @@
 
 namespace gp {
 
+std::atomic<long long> g_launch_count{0};
+
 // ------------------------------------------------------------------ memory
 
 void *dev_alloc(gp_ctx *ctx, size_t bytes) {
