@@ -223,6 +223,31 @@ gp_status gp_project(gp_ctx *ctx, int32_t n, const int32_t *cmap, const int32_t 
 gp_status gp_cut(gp_ctx *ctx, const gp_graph *g, const int32_t *blocks, int32_t k, int64_t *cut,
                  int64_t *block_weights);
 
+/*
+ * gp_cut without any allocation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory while they
+ * run -- a serving loop that reserved the whole device for its own arena up
+ * front, or a latency-critical path that cannot accept cudaMalloc's implicit
+ * device-wide synchronisation.  It needs no context and performs no
+ * cudaMalloc, cudaFree or other allocation: its only scratch is one fixed
+ * device array inside the library, present on every device that loads the
+ * library until the process exits.
+ *   g        graph in device memory (as for gp_cut)
+ *   blocks   device, g->n block ids in [0, k)
+ *   k        1 <= k <= GP_CUT_NOALLOC_MAX_K, else GP_ERR_INVALID
+ *   stream   cudaStream_t the work is ordered on; the call synchronises it
+ *   cut      host, receives the cut weight
+ *   block_weights  host array of k entries, or NULL
+ * Returns GP_ERR_INVALID for bad arguments or a block id outside [0, k),
+ * GP_ERR_CUDA when a CUDA call fails.  The first call on each device (with
+ * that device current) looks up the scratch array's device address once;
+ * make that first call before any stream capture on the device.  All calls
+ * share the scratch array: calls that overlap on the GPU race on it.
+ */
+#define GP_CUT_NOALLOC_MAX_K 4096
+gp_status gp_cut_noalloc(const gp_graph *g, const int32_t *blocks, int32_t k, void *stream,
+                         int64_t *cut, int64_t *block_weights);
+
 /* Frees a graph returned by gp_contract / gp_sparsify. */
 void gp_graph_release(gp_ctx *ctx, gp_graph *g);
 
