@@ -45,6 +45,14 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def workload_of(args):
+    if args.scale:
+        n = 1 << args.scale
+        return dict(name=f"erdos_renyi_n2^{args.scale}_m{10 * n}_k128", n=n, m=10 * n, k=128, eps=0.03,
+                    seed=1)
+    return SMALL if args.small else WORKLOAD
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -176,7 +184,7 @@ def run_reference(args, world, rank):
         cpu_sample_run(1)
     m, times = cpu_sample_run(args.steps)
     cb = cpu_baseline_obj(m, times)
-    w = SMALL if args.small else WORKLOAD
+    w = workload_of(args)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "edges/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
@@ -198,7 +206,7 @@ def run_gpu(args, world, rank, local):
     import paper_2504_17615_gb300 as gp
     from paper_2504_17615_gb300 import build as gpbuild
 
-    w = SMALL if args.small else WORKLOAD
+    w = workload_of(args)
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -240,6 +248,8 @@ def run_gpu(args, world, rank, local):
     for _ in range(args.steps):
         _, cut, st = step()
         stats.append((st.ms_coarsen, st.ms_initial, st.ms_uncoarsen, st.ms_total, cut, st.levels))
+    hierarchy = [[L["n"], L["m"], L["n_next"], L["m_coarse"], L["m_hat"], L["triggered"], L["m_next"]]
+                 for L in st.levels_list()] + [[st.n_coarsest]]
     ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -311,6 +321,8 @@ def run_gpu(args, world, rank, local):
             "partition_edges_per_s": world * g.m * args.steps / (step_ms / 1000.0),
             "phases_ms": {"coarsen": mean(0), "initial": mean(1), "uncoarsen": mean(2), "total": mean(3)},
             "cut": stats[-1][4], "levels": stats[-1][5],
+            "hierarchy": {"columns": ["n", "m", "n_next", "m_coarse", "m_hat", "triggered", "m_next"],
+                          "levels": hierarchy},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches // max(args.steps, 1),
             "gpu_launches_total": launches, "clocks": clk,
             "kernel_classes": {k: v for k, v in prof.items() if v["launches"]}}
@@ -326,6 +338,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--small", action="store_true", help="2^20-node graph (quick checks)")
+    ap.add_argument("--scale", type=int, default=None,
+                    help="ER graph with 2^S nodes and average degree 20 instead (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,

@@ -79,7 +79,7 @@ class gp_partition_stats(ctypes.Structure):
                 ("ms_initial", ctypes.c_double), ("ms_uncoarsen", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
 
-    def levels(self) -> list[dict]:
+    def levels_list(self) -> list[dict]:
         return [self.lv[i].as_dict() for i in range(self.levels)]
 
 

@@ -1,12 +1,21 @@
 // ip.cu -- initial partitioning of the coarsest graph by recursive
 // bisection (Sec. 4.3), plus the greedy rebalancer.
 //
-// All subproblems of one depth of the bisection tree are split together:
-// every (subproblem, trial) pair runs in its own thread block, growing side 1
-// greedily one node at a time (largest gain 2 conn(v) - deg'(v) among
-// frontier nodes that fit under L1, ties by the smallest id; otherwise the
-// node of smallest (h32(key(IP, 0, bid), v, t), v)) until side 1 reaches its
-// target weight.  The trial with the smallest cut (ties: lowest trial) wins.
+// All subproblems of one depth of the bisection tree are split together;
+// every (subproblem, trial) pair runs in its own warp.  A trial grows side 1
+// greedily one node at a time: among nodes that still fit under L1, the
+// frontier node (connected to side 1) of largest gain 2 conn(v) - deg'(v),
+// ties by the smallest id; when no frontier node fits, the node of smallest
+// (h32(key(IP, 0, bid), v, t), v).  It stops once side 1 weighs >= T1.  The
+// trial with the smallest cut (ties: lowest trial) wins.
+//
+// A step costs O(deg + n'/64), not O(n'): node lists are sorted by id, so
+// local index order is id order; every 64-node chunk keeps the largest key
+// (gain, -index) of its live frontier nodes, raised with a 64-bit atomicMax
+// when a neighbour's connection grows and recomputed only for the chunk of
+// the node just taken.  A picked node that no longer fits is retired for
+// good (side 1 only gets heavier), which leaves the choice among the nodes
+// that fit unchanged.
 #include "gp_internal.cuh"
 
 #include <algorithm>
@@ -15,8 +24,8 @@ namespace gp {
 
 namespace {
 
-constexpr int kIpThreads = 512;
-constexpr int kIpWarps = kIpThreads / 32;
+constexpr int kChunkNodes = 64;
+constexpr int kMaxSmemBytes = 227 * 1024;
 
 struct Sub {
   int32_t start, count;  // node list range
@@ -26,121 +35,125 @@ struct Sub {
 };
 
 struct IpArgs {
-  const int32_t *xadj, *adjncy, *adjwgt, *vwgt;
-  const int32_t *list, *loc, *sp, *dp;
+  const int32_t *xadj, *adjncy, *adjwgt;
+  const int32_t *vtx, *cvl, *dpl;  // by list position: node id, weight, deg'
+  const int2 *splo;                // by node: (subproblem, local index), subproblem -1 = done
+  const int32_t *dpv;              // by node: deg'
   const Sub *subs;
   int trials;
   int n;
   uint64_t seed;
-  int smem_nodes;          // subproblems up to this size keep their state in shared memory
-  int32_t *gconn;          // global fallback state, per block: stride entries
-  uint32_t *ghv;
+  int smem_nodes;                  // subproblems up to this size keep their state in shared memory
+  int32_t *gconn;                  // global fallback state per block
   uint8_t *gin;
-  int64_t gstride;
-  int64_t *trial_cut;      // per block
-  uint8_t *flags;          // [trial][n] side-1 flags by list position
+  unsigned long long *gbest;
+  int64_t gnodes, gchunks;
+  int64_t *trial_cut;              // per block
+  uint8_t *flags;                  // [trial][n] side-1 flag by list position
 };
 
-__device__ void block_best(int64_t &gain, int &vf, uint64_t &pn, int64_t *s_g, int *s_v, uint64_t *s_n) {
-  // frontier: max gain, then min v (vf < 0 = none); non-frontier: min packed (hv << 32 | v)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const int64_t g2 = __shfl_xor_sync(0xFFFFFFFFu, gain, o);
-    const int v2 = __shfl_xor_sync(0xFFFFFFFFu, vf, o);
-    const uint64_t p2 = __shfl_xor_sync(0xFFFFFFFFu, pn, o);
-    if (v2 >= 0 && (vf < 0 || g2 > gain || (g2 == gain && v2 < vf))) { gain = g2; vf = v2; }
-    pn = p2 < pn ? p2 : pn;
-  }
-  const int w = threadIdx.x >> 5;
-  if (lane_id() == 0) { s_g[w] = gain; s_v[w] = vf; s_n[w] = pn; }
-  __syncthreads();
-  gain = s_g[0]; vf = s_v[0]; pn = s_n[0];
-  for (int i = 1; i < kIpWarps; i++) {
-    if (s_v[i] >= 0 && (vf < 0 || s_g[i] > gain || (s_g[i] == gain && s_v[i] < vf))) {
-      gain = s_g[i]; vf = s_v[i];
-    }
-    pn = s_n[i] < pn ? s_n[i] : pn;
-  }
-  __syncthreads();
+__device__ __forceinline__ unsigned long long gain_key(int64_t gain, int j) {
+  return ((unsigned long long)(gain + 2147483648ll) << 32) | (0xFFFFFFFFu - (unsigned)j);
 }
 
-__global__ void __launch_bounds__(kIpThreads) k_ip_trial(IpArgs a) {
-  extern __shared__ unsigned char dyn[];
-  __shared__ int64_t s_g[kIpWarps];
-  __shared__ int s_v[kIpWarps];
-  __shared__ uint64_t s_n[kIpWarps];
-  __shared__ int64_t s_w1;
-  __shared__ int s_pick;
-  __shared__ unsigned long long s_cut;
+// chunk best over the live frontier nodes (state 0, conn > 0) of chunk c
+__device__ __forceinline__ void rescan_chunk(int c, int cnt, int start, const int32_t *conn,
+                                             const uint8_t *in1, const int32_t *dpl,
+                                             unsigned long long *best) {
+  const int lane = (int)lane_id();
+  unsigned long long b = 0;
+#pragma unroll
+  for (int r = 0; r < kChunkNodes / 32; r++) {
+    const int j = c * kChunkNodes + r * 32 + lane;
+    if (j < cnt && in1[j] == 0 && conn[j] > 0) {
+      const unsigned long long key = gain_key(2 * (int64_t)conn[j] - dpl[start + j], j);
+      b = key > b ? key : b;
+    }
+  }
+  b = warp_max(b);
+  if (lane == 0) best[c] = b;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int lane = (int)lane_id();
   const int si = blockIdx.x / a.trials, t = blockIdx.x % a.trials;
   const Sub S = a.subs[si];
-  const int cnt = S.count;
+  const int cnt = S.count, nch = (cnt + kChunkNodes - 1) / kChunkNodes;
+  unsigned long long *best;
   int32_t *conn;
-  uint32_t *hv;
   uint8_t *in1;
   if (cnt <= a.smem_nodes) {
-    conn = reinterpret_cast<int32_t *>(dyn);
-    hv = reinterpret_cast<uint32_t *>(dyn + sizeof(int32_t) * a.smem_nodes);
-    in1 = dyn + 2 * sizeof(int32_t) * a.smem_nodes;
+    const int mch = (a.smem_nodes + kChunkNodes - 1) / kChunkNodes;
+    best = reinterpret_cast<unsigned long long *>(dyn);
+    conn = reinterpret_cast<int32_t *>(dyn + sizeof(unsigned long long) * mch);
+    in1 = reinterpret_cast<uint8_t *>(conn + a.smem_nodes);
   } else {
-    conn = a.gconn + (int64_t)blockIdx.x * a.gstride;
-    hv = a.ghv + (int64_t)blockIdx.x * a.gstride;
-    in1 = a.gin + (int64_t)blockIdx.x * a.gstride;
+    best = a.gbest + (int64_t)blockIdx.x * a.gchunks;
+    conn = a.gconn + (int64_t)blockIdx.x * a.gnodes;
+    in1 = a.gin + (int64_t)blockIdx.x * a.gnodes;
   }
+  for (int j = lane; j < cnt; j += 32) { conn[j] = 0; in1[j] = 0; }
+  for (int c = lane; c < nch; c += 32) best[c] = 0;
+  __syncwarp();
   const uint64_t kip = stream_key(a.seed, TAG_IP, 0, (uint32_t)S.bid);
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    conn[j] = 0;
-    in1[j] = 0;
-    hv[j] = h32(kip, (uint32_t)a.list[S.start + j], (uint32_t)t);
-  }
-  if (threadIdx.x == 0) { s_w1 = 0; s_cut = 0; }
-  __syncthreads();
-  while (s_w1 < S.T1) {
-    const int64_t w1 = s_w1;
-    int64_t gain = 0;
-    int vf = -1;
-    uint64_t pn = ~0ull;
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      if (in1[j]) continue;
-      const int v = a.list[S.start + j];
-      if (w1 + a.vwgt[v] > S.L1) continue;
-      if (conn[j] > 0) {
-        const int64_t gj = 2 * (int64_t)conn[j] - a.dp[v];
-        if (vf < 0 || gj > gain || (gj == gain && v < vf)) { gain = gj; vf = v; }
-      } else {
-        const uint64_t p = ((uint64_t)hv[j] << 32) | (uint32_t)v;
-        pn = p < pn ? p : pn;
+  int64_t w1 = 0;
+  const int start = S.start;
+  while (w1 < S.T1) {
+    unsigned long long b = 0;
+    for (int c = lane; c < nch; c += 32) b = best[c] > b ? best[c] : b;
+    b = warp_max(b);
+    int j;
+    if (b != 0) {
+      j = (int)(0xFFFFFFFFu - (unsigned)(b & 0xFFFFFFFFull));
+      if (w1 + a.cvl[start + j] > S.L1) {  // cannot fit now, nor later: retire it
+        if (lane == 0) in1[j] = 2;
+        __syncwarp();
+        rescan_chunk(j / kChunkNodes, cnt, start, conn, in1, a.dpl, best);
+        continue;
       }
+    } else {
+      unsigned long long m = ~0ull;
+      for (int jj = lane; jj < cnt; jj += 32) {
+        if (in1[jj] != 0 || conn[jj] != 0 || w1 + a.cvl[start + jj] > S.L1) continue;
+        const unsigned long long key =
+            ((unsigned long long)h32(kip, (uint32_t)a.vtx[start + jj], (uint32_t)t) << 32) | (unsigned)jj;
+        m = key < m ? key : m;
+      }
+      m = warp_min(m);
+      if (m == ~0ull) break;
+      j = (int)(unsigned)(m & 0xFFFFFFFFull);
     }
-    block_best(gain, vf, pn, s_g, s_v, s_n);
-    const int pick = vf >= 0 ? vf : (pn != ~0ull ? (int)(uint32_t)pn : -1);
-    if (pick < 0) break;
-    if (threadIdx.x == 0) {
-      in1[a.loc[pick]] = 1;
-      s_w1 = w1 + a.vwgt[pick];
-    }
-    for (int e = a.xadj[pick] + threadIdx.x; e < a.xadj[pick + 1]; e += blockDim.x) {
+    w1 += a.cvl[start + j];
+    if (lane == 0) in1[j] = 1;
+    __syncwarp();
+    const int v = a.vtx[start + j];
+    for (int e = a.xadj[v] + lane; e < a.xadj[v + 1]; e += 32) {
       const int u = a.adjncy[e];
-      if (a.sp[u] == si) atomicAdd(&conn[a.loc[u]], a.adjwgt[e]);
+      const int2 sl = a.splo[u];
+      if (sl.x != si || in1[sl.y] != 0) continue;
+      const int nc = conn[sl.y] + a.adjwgt[e];
+      conn[sl.y] = nc;
+      atomicMax(&best[sl.y / kChunkNodes], gain_key(2 * (int64_t)nc - a.dpv[u], sl.y));
     }
-    __syncthreads();
+    __syncwarp();
+    rescan_chunk(j / kChunkNodes, cnt, start, conn, in1, a.dpl, best);
   }
   // cut of this trial inside the subproblem
   unsigned long long cut = 0;
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    if (!in1[j]) continue;
-    const int v = a.list[S.start + j];
+  for (int jj = lane; jj < cnt; jj += 32) {
+    if (in1[jj] != 1) continue;
+    const int v = a.vtx[start + jj];
     for (int e = a.xadj[v]; e < a.xadj[v + 1]; e++) {
-      const int u = a.adjncy[e];
-      if (a.sp[u] == si && !in1[a.loc[u]]) cut += (unsigned long long)a.adjwgt[e];
+      const int2 sl = a.splo[a.adjncy[e]];
+      if (sl.x == si && in1[sl.y] != 1) cut += (unsigned long long)a.adjwgt[e];
     }
   }
   cut = warp_sum(cut);
-  if (lane_id() == 0 && cut) atomicAdd(&s_cut, cut);
-  __syncthreads();
-  if (threadIdx.x == 0) a.trial_cut[blockIdx.x] = (int64_t)s_cut;
-  uint8_t *fl = a.flags + (int64_t)t * a.n + S.start;
-  for (int j = threadIdx.x; j < cnt; j += blockDim.x) fl[j] = in1[j];
+  if (lane == 0) a.trial_cut[blockIdx.x] = (int64_t)cut;
+  uint8_t *fl = a.flags + (int64_t)t * a.n + start;
+  for (int jj = lane; jj < cnt; jj += 32) fl[jj] = in1[jj] == 1;
 }
 
 __global__ void k_sub_count(const int32_t *sp, const int32_t *vwgt, int n, int32_t *cnt, long long *w) {
@@ -152,31 +165,44 @@ __global__ void k_sub_count(const int32_t *sp, const int32_t *vwgt, int n, int32
   }
 }
 
-__global__ void k_sub_fill(const int32_t *sp, int n, const int32_t *start, int32_t *cursor,
-                           int32_t *list, int32_t *loc) {
+// sort keys: live nodes by (subproblem, id) first, finished nodes after them
+__global__ void k_sub_keys(const int32_t *sp, int n, int ns, uint64_t *keys, uint32_t *vals) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int s = sp[v];
-    if (s < 0) continue;
-    const int p = atomicAdd(&cursor[s], 1);
-    list[start[s] + p] = v;
-    loc[v] = p;
+    keys[v] = ((uint64_t)(uint32_t)(s >= 0 ? s : ns) << 32) | (uint32_t)v;
+    vals[v] = 0;
   }
 }
 
-// deg'(v): weight to nodes of the same subproblem
-__global__ void k_dp(const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *sp,
-                     int n, int32_t *dp) {
+__global__ void k_sub_lists(const uint64_t *keys, int n, int live, const int32_t *start, const int32_t *vwgt,
+                            int32_t *vtx, int32_t *cvl, int2 *splo) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int v = (int)(uint32_t)keys[p];
+    if (p < live) {
+      const int s = (int)(keys[p] >> 32);
+      vtx[p] = v;
+      cvl[p] = vwgt[v];
+      splo[v] = make_int2(s, p - start[s]);
+    } else {
+      splo[v] = make_int2(-1, 0);
+    }
+  }
+}
+
+// deg'(v): weight to nodes of the same subproblem, one warp per listed node
+__global__ void k_sub_dp(const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *vtx,
+                         const int2 *splo, int live, int32_t *dpl, int32_t *dpv) {
   const int lane = (int)lane_id();
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int v = wid; v < n; v += nw) {
-    const int s = sp[v];
-    if (s < 0) continue;
+  for (int p = wid; p < live; p += nw) {
+    const int v = vtx[p];
+    const int s = splo[v].x;
     int sum = 0;
     for (int e = xadj[v] + lane; e < xadj[v + 1]; e += 32)
-      if (sp[adjncy[e]] == s) sum += adjwgt[e];
+      if (splo[adjncy[e]].x == s) sum += adjwgt[e];
     sum = warp_sum(sum);
-    if (lane == 0) dp[v] = sum;
+    if (lane == 0) { dpl[p] = sum; dpv[v] = sum; }
   }
 }
 
@@ -190,12 +216,12 @@ __global__ void k_ip_select(const int64_t *trial_cut, int nsubs, int trials, int
 }
 
 // children: child[2 s + side] = new subproblem index, or -(1 + block) when final
-__global__ void k_ip_assign(int n, const int32_t *loc, const int32_t *best, const uint8_t *flags,
-                            const int32_t *start, const int32_t *child, int32_t *sp, int32_t *blocks) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    const int s = sp[v];
-    if (s < 0) continue;
-    const int side1 = flags[(int64_t)best[s] * n + start[s] + loc[v]];
+__global__ void k_ip_assign(int n, int live, const int32_t *vtx, const int2 *splo, const int32_t *best,
+                            const uint8_t *flags, const int32_t *child, int32_t *sp, int32_t *blocks) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < live; p += gridDim.x * blockDim.x) {
+    const int v = vtx[p];
+    const int s = splo[v].x;
+    const int side1 = flags[(int64_t)best[s] * n + p];
     const int c = child[2 * s + (side1 ? 0 : 1)];
     if (c < 0) {
       blocks[v] = -(c + 1);
@@ -226,19 +252,21 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
   GP_CUDA(cudaMemsetAsync(blocks, 0, sizeof(int32_t) * (n > 0 ? n : 1), ctx->stream));
   if (k <= 1 || n == 0) return;
   const int grid = grid_for(n, 256, ctx->num_sms * 8);
-  DBuf<int32_t> sp(ctx, (size_t)n), list(ctx, (size_t)n), loc(ctx, (size_t)n), dp(ctx, (size_t)n);
+  DBuf<int32_t> sp(ctx, (size_t)n), vtx(ctx, (size_t)n), cvl(ctx, (size_t)n), dpl(ctx, (size_t)n),
+      dpv(ctx, (size_t)n);
+  DBuf<int2> splo(ctx, (size_t)n);
+  DBuf<uint64_t> keys(ctx, (size_t)n);
+  DBuf<uint32_t> vals(ctx, (size_t)n);
   sp.zero();  // everybody in subproblem 0
   const int64_t eps_l = eps_ppm / ceil_log2(k);
   std::vector<HostSub> subs{{k, 0, 1}};
-  int smem_nodes = 12000;
-  const size_t smem_bytes = (size_t)smem_nodes * 9;
-  GP_CUDA(cudaFuncSetAttribute(k_ip_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
+  GP_CUDA(cudaFuncSetAttribute(k_ip_grow, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes));
   DBuf<uint8_t> flags(ctx, (size_t)trials * n);
   while (!subs.empty()) {
     const int ns = (int)subs.size();
-    DBuf<int32_t> cnt(ctx, (size_t)ns), start(ctx, (size_t)ns + 1), cursor(ctx, (size_t)ns);
+    DBuf<int32_t> cnt(ctx, (size_t)ns), start(ctx, (size_t)ns + 1);
     DBuf<long long> wsum(ctx, (size_t)ns);
-    cnt.zero(); wsum.zero(); cursor.zero();
+    cnt.zero(); wsum.zero();
     k_sub_count<<<grid, 256, 0, ctx->stream>>>(sp.get(), g.vwgt, n, cnt.get(), wsum.get());
     GP_LAUNCH_CHECK();
     std::vector<int32_t> hc(ns);
@@ -248,12 +276,17 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
     std::vector<int32_t> hs(ns + 1);
     hs[0] = 0;
     for (int i = 0; i < ns; i++) hs[i + 1] = hs[i] + hc[i];
+    const int live = hs[ns];
     GP_CUDA(cudaMemcpyAsync(start.get(), hs.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice,
                             ctx->stream));
-    k_sub_fill<<<grid, 256, 0, ctx->stream>>>(sp.get(), n, start.get(), cursor.get(), list.get(), loc.get());
+    k_sub_keys<<<grid, 256, 0, ctx->stream>>>(sp.get(), n, ns, keys.get(), vals.get());
     GP_LAUNCH_CHECK();
-    k_dp<<<grid_for((int64_t)n * 32, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(
-        g.xadj, g.adjncy, g.adjwgt, sp.get(), n, dp.get());
+    radix_sort_pairs(ctx, keys.get(), vals.get(), n, 32 + 1 + ceil_log2(ns + 1));
+    k_sub_lists<<<grid, 256, 0, ctx->stream>>>(keys.get(), n, live, start.get(), g.vwgt, vtx.get(), cvl.get(),
+                                                splo.get());
+    GP_LAUNCH_CHECK();
+    k_sub_dp<<<grid_for((int64_t)live * 32, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+        g.xadj, g.adjncy, g.adjwgt, vtx.get(), splo.get(), live, dpl.get(), dpv.get());
     GP_LAUNCH_CHECK();
     std::vector<Sub> hsub(ns);
     int maxcnt = 0;
@@ -272,23 +305,29 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
     GP_CUDA(cudaMemcpyAsync(dsub.get(), hsub.data(), sizeof(Sub) * ns, cudaMemcpyHostToDevice, ctx->stream));
     const int nblocks = ns * trials;
     DBuf<int64_t> tcut(ctx, (size_t)nblocks);
-    DBuf<int32_t> gconn;
-    DBuf<uint32_t> ghv;
-    DBuf<uint8_t> gin;
     IpArgs a{};
-    a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
-    a.list = list.get(); a.loc = loc.get(); a.sp = sp.get(); a.dp = dp.get(); a.subs = dsub.get();
-    a.trials = trials; a.n = n; a.seed = seed; a.smem_nodes = smem_nodes;
-    if (maxcnt > smem_nodes) {
-      a.gstride = maxcnt;
-      gconn.reset(ctx, (size_t)nblocks * maxcnt);
-      ghv.reset(ctx, (size_t)nblocks * maxcnt);
-      gin.reset(ctx, (size_t)nblocks * maxcnt);
-      a.gconn = gconn.get(); a.ghv = ghv.get(); a.gin = gin.get();
+    a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt;
+    a.vtx = vtx.get(); a.cvl = cvl.get(); a.dpl = dpl.get(); a.splo = splo.get(); a.dpv = dpv.get();
+    a.subs = dsub.get(); a.trials = trials; a.n = n; a.seed = seed;
+    // shared-memory state: chunk maxima (8 B per 64 nodes) + conn (4 B) + state (1 B) per node
+    const int smem_cap = (kMaxSmemBytes - 64) * kChunkNodes / (8 + 5 * kChunkNodes);
+    a.smem_nodes = std::max(1, std::min(maxcnt, smem_cap));
+    const size_t smem_bytes = (size_t)((a.smem_nodes + kChunkNodes - 1) / kChunkNodes) * 8 +
+                              (size_t)a.smem_nodes * 5;
+    DBuf<int32_t> gconn;
+    DBuf<uint8_t> gin;
+    DBuf<unsigned long long> gbest;
+    if (maxcnt > a.smem_nodes) {
+      a.gnodes = maxcnt;
+      a.gchunks = (maxcnt + kChunkNodes - 1) / kChunkNodes;
+      gconn.reset(ctx, (size_t)nblocks * a.gnodes);
+      gin.reset(ctx, (size_t)nblocks * a.gnodes);
+      gbest.reset(ctx, (size_t)nblocks * a.gchunks);
+      a.gconn = gconn.get(); a.gin = gin.get(); a.gbest = gbest.get();
     }
     a.trial_cut = tcut.get();
     a.flags = flags.get();
-    k_ip_trial<<<nblocks, kIpThreads, smem_bytes, ctx->stream>>>(a);
+    k_ip_grow<<<nblocks, 32, smem_bytes, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
     DBuf<int32_t> best(ctx, (size_t)ns), child(ctx, (size_t)2 * ns);
     k_ip_select<<<grid_for(ns, 128, 1024), 128, 0, ctx->stream>>>(tcut.get(), ns, trials, best.get());
@@ -311,7 +350,7 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
     }
     GP_CUDA(cudaMemcpyAsync(child.get(), hchild.data(), sizeof(int32_t) * 2 * ns, cudaMemcpyHostToDevice,
                             ctx->stream));
-    k_ip_assign<<<grid, 256, 0, ctx->stream>>>(n, loc.get(), best.get(), flags.get(), start.get(),
+    k_ip_assign<<<grid, 256, 0, ctx->stream>>>(n, live, vtx.get(), splo.get(), best.get(), flags.get(),
                                                 child.get(), sp.get(), blocks);
     GP_LAUNCH_CHECK();
     GP_CUDA(cudaStreamSynchronize(ctx->stream));  // host vectors above must outlive the copies

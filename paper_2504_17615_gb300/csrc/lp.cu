@@ -70,47 +70,125 @@ __device__ __forceinline__ void emit(const RateArgs &a, int i, int v, int best, 
   }
 }
 
-// ------------------------------------------------ degree <= 32: warp/node
+// ------------------------------------- degree <= 32: G lanes per node
+//
+// A warp rates 32/G nodes side by side (one neighbour per lane of a G-lane
+// group) and keeps U such sets in flight, issuing the loads of all U*32/G
+// nodes phase by phase (offsets, neighbours, labels) so that independent
+// dependency chains overlap.  Equal labels within a group are summed in a
+// 2G-slot shared-memory table per group (the first lane to claim a slot is
+// the label's leader).  The choice is lazy in the label weights: candidates
+// are ranked by (rating, tie hash, label) without the bound, and only the
+// leading candidate's weight is fetched; if it does not fit, it is dropped
+// and the next one is tried.  This picks exactly the best admissible
+// candidate while reading one label weight per node in the usual case, and
+// none at all when no neighbouring label beats the node's own label.
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_rate_small(RateArgs a) {
+template <int MODE, int G, int U>
+__global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
+  static_assert(G == 8 || G == 16 || G == 32, "group width");
+  constexpr int NV = 32 / G;
+  constexpr int PER = NV * U;
+  constexpr int TS = 2 * G;  // table slots per group
+  __shared__ int s_tk[kWarpsPerBlock][U * 64];
+  __shared__ int s_tv[kWarpsPerBlock][U * 64];
   if (a.stop && *a.stop) return;
+  const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane % G;
+  const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
+  for (int t = lane; t < U * 64; t += 32) { s_tk[wib][t] = -1; s_tv[wib][t] = 0; }
+  __syncwarp();
   const int begin = a.offs[a.key], end = a.offs[a.key + 1];
-  const int lane = (int)lane_id();
   const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
-  for (int i = begin + wid; i < end; i += nw) {
-    const int v = a.list[i];
-    const int start = a.xadj[v];
-    const int deg = a.xadj[v + 1] - start;
-    const int own = a.label[v];
-    const int cv = a.vwgt[v];
-    const bool valid = lane < deg;
-    int L = 0, w = 0;
-    if (valid) {
-      L = a.label[a.adjncy[start + lane]];
-      w = a.adjwgt[start + lane];
+  for (int base = begin + wid * PER; base < end; base += nw * PER) {
+    int v[U], st[U], deg[U], own[U], cv[U], L[U], w[U], u[U];
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      const int i = base + q * NV + grp;
+      v[q] = i < end ? a.list[i] : -1;
     }
-    const unsigned key = valid ? (unsigned)L : (0x80000000u | (unsigned)lane);
-    const unsigned peers = __match_any_sync(FULL, key);
-    const int sum = __reduce_add_sync(peers, w);
-    const bool leader = valid && lane == __ffs(peers) - 1;
-    const int own_r = __reduce_max_sync(FULL, (leader && L == own) ? sum : 0);
-    bool cand = leader && L != own;
-    const unsigned ncand = __popc(__ballot_sync(FULL, cand));
-    if (MODE == RATE_LP && cand) cand = (int64_t)a.weight[L] + cv <= a.bound;
-    const int rmax = __reduce_max_sync(FULL, cand ? sum : -1);
-    ue += deg; uv += 1; uc += ncand;
-    if (rmax < 0 || (MODE == RATE_LP && rmax <= own_r)) continue;
-    const bool top = cand && sum == rmax;
-    const unsigned h = top ? h32(a.ktie, (uint32_t)v, (uint32_t)L) : 0xFFFFFFFFu;
-    const unsigned hmin = __reduce_min_sync(FULL, h);
-    const unsigned best = __reduce_min_sync(FULL, (top && h == hmin) ? (unsigned)L : 0xFFFFFFFFu);
-    if (lane == 0) emit<MODE>(a, i, v, (int)best, cv);
-    up += 1;
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      const bool ok = v[q] >= 0;
+      const int vv = ok ? v[q] : 0;
+      st[q] = a.xadj[vv];
+      deg[q] = ok ? a.xadj[vv + 1] - st[q] : 0;
+      own[q] = ok ? a.label[vv] : -2;
+      cv[q] = a.vwgt[vv];
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      const bool ok = gl < deg[q];
+      u[q] = ok ? a.adjncy[st[q] + gl] : -1;
+      w[q] = ok ? a.adjwgt[st[q] + gl] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) L[q] = u[q] >= 0 ? a.label[u[q]] : -1;
+    // sum equal labels per group in the shared tables
+    int slot[U];
+    bool lead[U];
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      int *tk = &s_tk[wib][q * 64 + grp * TS];
+      slot[q] = -1;
+      lead[q] = false;
+      if (u[q] >= 0) {
+        unsigned sl = ((unsigned)L[q] * 2654435761u) >> (32 - (G == 8 ? 4 : G == 16 ? 5 : 6));
+        for (int p = 0; p < TS; p++) {  // bounded: a group has at most G labels in 2G slots
+          const int prev = atomicCAS(&tk[sl], -1, L[q]);
+          if (prev == -1) { lead[q] = true; break; }
+          if (prev == L[q]) break;
+          sl = (sl + 1) & (TS - 1);
+        }
+        slot[q] = q * 64 + grp * TS + (int)sl;
+        atomicAdd(&s_tv[wib][slot[q]], w[q]);
+      }
+    }
+    __syncwarp();
+    int sum[U];
+#pragma unroll
+    for (int q = 0; q < U; q++) sum[q] = slot[q] >= 0 ? s_tv[wib][slot[q]] : 0;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < U; q++)
+      if (lead[q]) { s_tk[wib][slot[q]] = -1; s_tv[wib][slot[q]] = 0; }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      const int own_r = __reduce_max_sync(gmask, (lead[q] && L[q] == own[q]) ? sum[q] : 0);
+      bool alive = lead[q] && L[q] != own[q];
+      uc += alive;
+      unsigned best = 0xFFFFFFFFu;
+      bool searching = v[q] >= 0;
+      while (__any_sync(FULL, searching)) {
+        const int r = __reduce_max_sync(gmask, (searching && alive) ? sum[q] : -1);
+        if (r < 0 || (MODE == RATE_LP && r <= own_r)) searching = false;
+        const bool top = searching && alive && sum[q] == r;
+        const unsigned h = top ? h32(a.ktie, (uint32_t)v[q], (uint32_t)L[q]) : 0xFFFFFFFFu;
+        const unsigned hmin = __reduce_min_sync(gmask, h);
+        const unsigned c = __reduce_min_sync(gmask, (top && h == hmin) ? (unsigned)L[q] : 0xFFFFFFFFu);
+        if (MODE != RATE_LP) {
+          if (searching) { best = c; searching = false; }
+        } else {
+          const bool holder = top && h == hmin && (unsigned)L[q] == c;
+          const unsigned fits = holder && (int64_t)a.weight[c] + cv[q] <= a.bound ? 1u : 0u;
+          if (searching && __reduce_or_sync(gmask, fits)) { best = c; searching = false; }
+          alive = alive && (unsigned)L[q] != c;
+        }
+      }
+      if (gl == 0 && v[q] >= 0) {
+        ue += deg[q];
+        uv += 1;
+        if (best != 0xFFFFFFFFu) {
+          emit<MODE>(a, base + q * NV + grp, v[q], (int)best, cv[q]);
+          up += 1;
+        }
+      }
+    }
   }
-  add_units(a.units, lane == 0 ? ue : 0, lane == 0 ? uv : 0, lane == 0 ? uc : 0, lane == 0 ? up : 0);
+  add_units(a.units, ue, uv, uc, up);
 }
 
 // --------------------------------------- degree <= 128: warp/node + table
@@ -576,12 +654,18 @@ template <int MODE>
 void launch_rate(gp_ctx *ctx, RateArgs a, int bucket_key_base, const RateTables &t) {
   const int grid_w = ctx->num_sms * 8;
   a.key = bucket_key_base + 0;
-  k_rate_small<MODE><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  k_rate_group<MODE, 8, 2><<<grid_w, kThreads, 0, ctx->stream>>>(a);
   GP_LAUNCH_CHECK();
   a.key = bucket_key_base + 1;
-  k_rate_medium<MODE><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  k_rate_group<MODE, 16, 2><<<grid_w, kThreads, 0, ctx->stream>>>(a);
   GP_LAUNCH_CHECK();
   a.key = bucket_key_base + 2;
+  k_rate_group<MODE, 32, 4><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  GP_LAUNCH_CHECK();
+  a.key = bucket_key_base + 3;
+  k_rate_medium<MODE><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  GP_LAUNCH_CHECK();
+  a.key = bucket_key_base + 4;
   a.gkeys = t.gkeys.get();
   a.gvals = t.gvals.get();
   a.gstride = t.stride;

@@ -5,14 +5,15 @@
 
 namespace gp {
 
-// Degree classes of the rating kernels.
-constexpr int kNumBuckets = 3;
-constexpr int kSmallMaxDeg = 32;    // one warp, one neighbour per lane
-constexpr int kMediumMaxDeg = 128;  // one warp, shared-memory table of 256 slots
-constexpr int kLargeSmemSlots = 4096;  // one block; bigger tables live in global memory
+// Degree classes of the rating kernels: <= 8, <= 16, <= 32 (8/16/32 lanes per
+// node, one neighbour per lane), <= 128 (a warp with a 256-slot shared table),
+// larger (a block with a shared table, or a global one beyond 2048).
+constexpr int kNumBuckets = 5;
+constexpr int kMediumMaxDeg = 128;
+constexpr int kLargeSmemSlots = 4096;
 
 __host__ __device__ __forceinline__ int degree_bucket(int deg) {
-  return deg <= kSmallMaxDeg ? 0 : (deg <= kMediumMaxDeg ? 1 : 2);
+  return deg <= 8 ? 0 : deg <= 16 ? 1 : deg <= 32 ? 2 : deg <= kMediumMaxDeg ? 3 : 4;
 }
 
 enum RateMode { RATE_LP = 0, RATE_FAV = 1 };
