@@ -320,7 +320,8 @@ def run_gpu(args, world, rank, local):
                        "value_is": "input edges / coarsening-phase device time"},
             "partition_edges_per_s": world * g.m * args.steps / (step_ms / 1000.0),
             "phases_ms": {"coarsen": mean(0), "initial": mean(1), "uncoarsen": mean(2), "total": mean(3)},
-            "cut": stats[-1][4], "levels": stats[-1][5],
+            "cut": stats[-1][4], "levels": stats[-1][5], "ip_cut": st.ip_cut,
+            "rebalance_moves": st.rebalance_moves, "n_coarsest": st.n_coarsest,
             "hierarchy": {"columns": ["n", "m", "n_next", "m_coarse", "m_hat", "triggered", "m_next"],
                           "levels": hierarchy},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches // max(args.steps, 1),

@@ -564,18 +564,42 @@ typedef struct {
   int32_t *loc;  /* position of each node in its subproblem's node list */
 } ip_ctx;
 
+typedef struct { int64_t gain; int32_t j; } gain_t;
+
+static int gain_cmp(const void *a, const void *b) {
+  const gain_t *x = (const gain_t *)a, *y = (const gain_t *)b;
+  if (x->gain != y->gain) return x->gain > y->gain ? -1 : 1;
+  return (x->j > y->j) - (x->j < y->j);
+}
+
 /*
  * Recursive bisection of the coarsest graph (Sec. 4.3; the bipartitioner
  * is not specified in the paper, R18).  Subproblem (nodes V', k' blocks
  * starting at b0, heap id bid): k1 = ceil(k'/2) blocks go to side 1 with
  * target T1 = ceil(c(V') k1 / k') and limit L1 = floor(T1 (1e6 + eps') / 1e6),
  * eps' = eps_ppm / ceil(log2 k).  Each of the trials grows side 1 greedily
- * from empty: among nodes that still fit under L1, take the frontier node
- * (connected to side 1) of largest gain 2 conn(v) - deg'(v) (ties: smallest
- * id), else the non-frontier node of smallest (h32(key(IP, 0, bid), v, t), v);
- * stop once side 1 weighs >= T1 or nothing fits.  The trial with the
+ * from empty in steps: the frontier nodes (connected to side 1) that fit
+ * under L1 at the start of a step are ranked by gain 2 conn(v) - deg'(v)
+ * (desc, ties: smallest id) and taken in that order while they still fit,
+ * at most B = 1 + |V'| / 1024 of them per step (one at a time below 1024
+ * nodes); with no such frontier node the step takes the node of smallest
+ * (h32(key(IP, 0, bid), v, t), v) that fits.  Growing stops once side 1
+ * weighs >= T1 or nothing fits.  The trial with the
  * smallest cut (ties: lowest t) wins; recurse on both sides.
  */
+/* moves local node j to side 1 and raises its neighbours' connection */
+static void add_to_side1(ip_ctx *C, uint32_t bid, int32_t j, const int32_t *V, char *in1, int64_t *conn,
+                         int64_t *w1) {
+  const og *g = C->g;
+  int32_t v = V[j];
+  in1[j] = 1;
+  *w1 += g->vwgt[v];
+  for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; e++) {
+    int32_t u = g->adjncy[e];
+    if (C->mark[u] == (int32_t)bid) conn[C->loc[u]] += g->adjwgt[e];
+  }
+}
+
 static void ip_bisect(ip_ctx *C, int32_t *V, int32_t nv, int32_t kk, int32_t b0, uint32_t bid) {
   const og *g = C->g;
   if (nv == 0) return;
@@ -598,6 +622,8 @@ static void ip_bisect(ip_ctx *C, int32_t *V, int32_t nv, int32_t kk, int32_t b0,
   uint32_t *hv = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)nv);
   char *in1 = (char *)malloc((size_t)nv);
   char *best_in1 = (char *)malloc((size_t)nv);
+  gain_t *F = (gain_t *)malloc(sizeof(gain_t) * ((size_t)nv + 1));
+  const int64_t B = 1 + nv / 1024; /* nodes taken per growing step */
   for (int32_t j = 0; j < nv; j++) {
     int32_t v = V[j];
     for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; e++)
@@ -613,25 +639,31 @@ static void ip_bisect(ip_ctx *C, int32_t *V, int32_t nv, int32_t kk, int32_t b0,
     }
     int64_t w1 = 0;
     while (w1 < T1) {
-      int32_t bf = -1, bn = -1;
-      int64_t bf_gain = 0;
+      /* the admissible frontier at the start of the step, by (gain desc, id asc) */
+      int32_t nf = 0, bn = -1;
       for (int32_t j = 0; j < nv; j++) {
         if (in1[j] || w1 + g->vwgt[V[j]] > L1) continue;
         if (conn[j] > 0) {
-          int64_t gain = 2 * conn[j] - Dp[j];
-          if (bf < 0 || gain > bf_gain) { bf = j; bf_gain = gain; }
+          F[nf].gain = 2 * conn[j] - Dp[j];
+          F[nf].j = j;
+          nf++;
         } else if (bn < 0 || hv[j] < hv[bn]) {
           bn = j;
         }
       }
-      int32_t pick = bf >= 0 ? bf : bn;
-      if (pick < 0) break;
-      in1[pick] = 1;
-      w1 += g->vwgt[V[pick]];
-      int32_t v = V[pick];
-      for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; e++) {
-        int32_t u = g->adjncy[e];
-        if (C->mark[u] == (int32_t)bid) conn[C->loc[u]] += g->adjwgt[e];
+      if (nf > 0) {
+        qsort(F, (size_t)nf, sizeof(gain_t), gain_cmp);
+        int64_t taken = 0;
+        for (int32_t f = 0; f < nf && taken < B && w1 < T1; f++) {
+          int32_t j = F[f].j;
+          if (w1 + g->vwgt[V[j]] > L1) continue; /* no longer fits (nor ever will) */
+          add_to_side1(C, bid, j, V, in1, conn, &w1);
+          taken++;
+        }
+      } else if (bn >= 0) {
+        add_to_side1(C, bid, bn, V, in1, conn, &w1);
+      } else {
+        break;
       }
     }
     int64_t cut = 0;
@@ -654,7 +686,7 @@ static void ip_bisect(ip_ctx *C, int32_t *V, int32_t nv, int32_t kk, int32_t b0,
   for (int32_t j = 0; j < nv; j++) {
     if (best_in1[j]) V1[n1++] = V[j]; else V2[n2++] = V[j];
   }
-  free(Dp); free(conn); free(hv); free(in1); free(best_in1);
+  free(Dp); free(conn); free(hv); free(in1); free(best_in1); free(F);
   ip_bisect(C, V1, n1, k1, b0, 2 * bid);
   ip_bisect(C, V2, n2, k2, b0 + k1, 2 * bid + 1);
   free(V1); free(V2);

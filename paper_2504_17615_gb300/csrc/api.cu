@@ -45,7 +45,8 @@ gp_config cfg_or_default(const gp_config *cfg) {
 const char *kProfNames[gp::PROF_COUNT_] = {
     "lp_rate",  "lp_accept", "refine_rate", "refine_accept", "round_setup", "two_hop",
     "relabel",  "contract",  "contract_aux", "sparsify",     "initial",     "project",
-    "cut",      "validate",  "sort",         "scan"};
+    "cut",      "validate",  "sort",         "scan",          "lp_overflow", "lp_apply",
+    "refine_overflow", "refine_apply", "rebalance"};
 
 }  // namespace
 

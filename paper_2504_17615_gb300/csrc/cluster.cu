@@ -106,6 +106,7 @@ __global__ void k_cmap(const int32_t *label, const int32_t *rank, int n, int32_t
 
 void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uint64_t seed,
                    const gp_config &cfg, int32_t *cmap, int32_t *label_out, LevelOut &out) {
+  TraceTimer trace(ctx);
   const int n = g.n;
   const int grid = grid_for(n, 256, ctx->num_sms * 8);
   DBuf<int32_t> label_own;
@@ -128,6 +129,7 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
   p.bound = U; p.count_clusters = true; p.n_min = n_min;
   p.dbg_max_subrounds = cfg.dbg_max_subrounds;
   p.prof_rate = PROF_LP_RATE; p.prof_accept = PROF_LP_ACCEPT;
+  p.prof_overflow = PROF_LP_OVERFLOW; p.prof_apply = PROF_LP_APPLY;
   LpResult r = lp_run(ctx, g, label, cw.get(), size.get(), n, seed, p, ncl_dev.get());
   int64_t ncl = n == 0 ? 0 : r.nclusters;
   out.st.n = n;
@@ -204,6 +206,9 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
     out.n_coarse = read_scalar(ctx, total.get());
   }
   out.st.n_next = out.n_coarse;
+  if (trace.on())
+    fprintf(stderr, "[gp coarsen] level=%d n=%d -> %d (lp %lld, 2hop %lld) ms=%.2f\n", level, n, out.n_coarse,
+            (long long)out.st.clusters_lp, (long long)out.st.clusters_2hop, trace.ms());
 }
 
 }  // namespace gp

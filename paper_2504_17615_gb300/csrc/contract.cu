@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_rows(const int32_t *tstart, c
 }  // namespace
 
 void contract_graph(gp_ctx *ctx, const DevGraph &g, const int32_t *cmap, int32_t nc, DevGraph &out) {
+  TraceTimer trace(ctx);
   const int n = g.n;
   const int grid = grid_for(n, 256, ctx->num_sms * 8);
   DBuf<int32_t> cnt(ctx, (size_t)nc + 1), ub(ctx, (size_t)nc + 1), cw(ctx, (size_t)nc + 1);
@@ -298,6 +299,9 @@ void contract_graph(gp_ctx *ctx, const DevGraph &g, const int32_t *cmap, int32_t
   }
   out.bv.reset(ctx, (size_t)nc);
   out.vwgt = out.bv.get();
+  if (trace.on())
+    fprintf(stderr, "[gp contract] n=%d m2=%lld -> n=%d m2=%lld ms=%.2f\n", n, (long long)g.m2, nc,
+            (long long)out.m2, trace.ms());
   if (nc > 0)
     GP_CUDA(cudaMemcpyAsync(out.vwgt, cw.get(), sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice,
                             ctx->stream));

@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -51,9 +52,9 @@ extern std::atomic<long long> g_launch_count;
 
 enum ProfClass {
   PROF_LP_RATE = 0,   // clustering LP: rate + choose (the dominant kernel)
-  PROF_LP_ACCEPT,     // clustering LP: acceptance + apply
+  PROF_LP_ACCEPT,     // clustering LP: acceptance decision
   PROF_REF_RATE,      // refinement LP: rate + choose
-  PROF_REF_ACCEPT,    // refinement LP: acceptance + apply
+  PROF_REF_ACCEPT,    // refinement LP: acceptance decision
   PROF_ROUND_SETUP,   // per-round activity bucketing
   PROF_TWOHOP,        // 2-hop favourites + packing, isolated packing
   PROF_RELABEL,
@@ -66,6 +67,11 @@ enum ProfClass {
   PROF_VALIDATE,
   PROF_SORT,
   PROF_SCAN,
+  PROF_LP_OVERFLOW,   // clustering LP: ordering the proposers of overflowing targets
+  PROF_LP_APPLY,      // clustering LP: apply moves, count emptied clusters
+  PROF_REF_OVERFLOW,
+  PROF_REF_APPLY,
+  PROF_REBALANCE,     // greedy rebalance after the initial partition
   PROF_COUNT_
 };
 
@@ -163,6 +169,31 @@ struct ProfScope {
   cudaEvent_t a = nullptr;
   ProfScope(gp_ctx *c, int k);
   ~ProfScope();
+};
+
+// Wall time of a stretch of stream work, measured only when the GP_TRACE
+// environment variable is set (diagnostic output on stderr).
+struct TraceTimer {
+  gp_ctx *ctx;
+  cudaEvent_t a = nullptr, b = nullptr;
+  explicit TraceTimer(gp_ctx *c) : ctx(c) {
+    if (!getenv("GP_TRACE")) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { a = b = nullptr; return; }
+    cudaEventRecord(a, ctx->stream);
+  }
+  bool on() const { return a != nullptr; }
+  double ms() {
+    if (!a) return 0;
+    float f = 0;
+    cudaEventRecord(b, ctx->stream);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&f, a, b);
+    return f;
+  }
+  ~TraceTimer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
 };
 
 // ---------------------------------------------------------------- launch

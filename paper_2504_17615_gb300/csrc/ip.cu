@@ -3,13 +3,17 @@
 //
 // All subproblems of one depth of the bisection tree are split together;
 // every (subproblem, trial) pair runs in its own warp.  A trial grows side 1
-// greedily one node at a time: among nodes that still fit under L1, the
-// frontier node (connected to side 1) of largest gain 2 conn(v) - deg'(v),
-// ties by the smallest id; when no frontier node fits, the node of smallest
-// (h32(key(IP, 0, bid), v, t), v).  It stops once side 1 weighs >= T1.  The
-// trial with the smallest cut (ties: lowest trial) wins.
+// greedily: among nodes that still fit under L1, frontier nodes (connected
+// to side 1) of largest gain 2 conn(v) - deg'(v), ties by the smallest id;
+// when no frontier node fits, the node of smallest (h32(key(IP, 0, bid), v,
+// t), v).  It stops once side 1 weighs >= T1.  The trial with the smallest
+// cut (ties: lowest trial) wins.
 //
-// A step costs O(deg + n'/64), not O(n'): node lists are sorted by id, so
+// Each growing step takes up to B = 1 + n'/1024 frontier nodes in order of
+// their gains at the start of the step, skipping those that no longer fit
+// (one node per step below 1024 nodes).
+//
+// A node costs O(deg + n'/64), not O(n'): node lists are sorted by id, so
 // local index order is id order; every 64-node chunk keeps the largest key
 // (gain, -index) of its live frontier nodes, raised with a 64-bit atomicMax
 // when a neighbour's connection grows and recomputed only for the chunk of
@@ -34,20 +38,28 @@ struct Sub {
   int64_t T1, L1;        // side-1 target and limit
 };
 
+// Per-node state of a trial: S_FREE not connected to side 1, S_FRONT free and
+// connected, S_ONE in side 1, S_OUT retired (can never fit again).
+enum : uint8_t { S_FREE = 0, S_ONE = 1, S_OUT = 2, S_FRONT = 3 };
+
 struct IpArgs {
-  const int32_t *xadj, *adjncy, *adjwgt;
+  const int32_t *lxadj;            // local CSR of every subproblem (by list position)
+  const int2 *ladj;                // (local index, weight) of internal neighbours
   const int32_t *vtx, *cvl, *dpl;  // by list position: node id, weight, deg'
-  const int2 *splo;                // by node: (subproblem, local index), subproblem -1 = done
-  const int32_t *dpv;              // by node: deg'
   const Sub *subs;
   int trials;
   int n;
   uint64_t seed;
   int smem_nodes;                  // subproblems up to this size keep their state in shared memory
-  int32_t *gconn;                  // global fallback state per block
-  uint8_t *gin;
+  int cv16;                        // node weights fit 16 bits: kept in shared memory too
+  int32_t *gg;                     // global fallback state per block
+  uint8_t *gst;
+  uint16_t *gcv;
   unsigned long long *gbest;
   int64_t gnodes, gchunks;
+  int32_t *gbatch;                 // per block: the nodes taken in the current step
+  int batch_cap;
+  unsigned long long *trace;       // optional: [0] growing steps, [1] fallback scans, [2] retired nodes
   int64_t *trial_cut;              // per block
   uint8_t *flags;                  // [trial][n] side-1 flag by list position
 };
@@ -56,17 +68,16 @@ __device__ __forceinline__ unsigned long long gain_key(int64_t gain, int j) {
   return ((unsigned long long)(gain + 2147483648ll) << 32) | (0xFFFFFFFFu - (unsigned)j);
 }
 
-// chunk best over the live frontier nodes (state 0, conn > 0) of chunk c
-__device__ __forceinline__ void rescan_chunk(int c, int cnt, int start, const int32_t *conn,
-                                             const uint8_t *in1, const int32_t *dpl,
+// chunk best over the live frontier nodes of chunk c (shared-memory state only)
+__device__ __forceinline__ void rescan_chunk(int c, int cnt, const int32_t *g, const uint8_t *st,
                                              unsigned long long *best) {
   const int lane = (int)lane_id();
   unsigned long long b = 0;
 #pragma unroll
   for (int r = 0; r < kChunkNodes / 32; r++) {
     const int j = c * kChunkNodes + r * 32 + lane;
-    if (j < cnt && in1[j] == 0 && conn[j] > 0) {
-      const unsigned long long key = gain_key(2 * (int64_t)conn[j] - dpl[start + j], j);
+    if (j < cnt && st[j] == S_FRONT) {
+      const unsigned long long key = gain_key(g[j], j);
       b = key > b ? key : b;
     }
   }
@@ -81,79 +92,126 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
   const int si = blockIdx.x / a.trials, t = blockIdx.x % a.trials;
   const Sub S = a.subs[si];
   const int cnt = S.count, nch = (cnt + kChunkNodes - 1) / kChunkNodes;
+  const int start = S.start;
   unsigned long long *best;
-  int32_t *conn;
-  uint8_t *in1;
+  int32_t *g;
+  uint8_t *st;
+  uint16_t *cv = nullptr;
   if (cnt <= a.smem_nodes) {
     const int mch = (a.smem_nodes + kChunkNodes - 1) / kChunkNodes;
     best = reinterpret_cast<unsigned long long *>(dyn);
-    conn = reinterpret_cast<int32_t *>(dyn + sizeof(unsigned long long) * mch);
-    in1 = reinterpret_cast<uint8_t *>(conn + a.smem_nodes);
+    g = reinterpret_cast<int32_t *>(dyn + sizeof(unsigned long long) * mch);
+    if (a.cv16) cv = reinterpret_cast<uint16_t *>(g + a.smem_nodes);
+    st = reinterpret_cast<uint8_t *>(g + a.smem_nodes) + (a.cv16 ? 2 * a.smem_nodes : 0);
   } else {
     best = a.gbest + (int64_t)blockIdx.x * a.gchunks;
-    conn = a.gconn + (int64_t)blockIdx.x * a.gnodes;
-    in1 = a.gin + (int64_t)blockIdx.x * a.gnodes;
+    g = a.gg + (int64_t)blockIdx.x * a.gnodes;
+    st = a.gst + (int64_t)blockIdx.x * a.gnodes;
+    if (a.cv16) cv = a.gcv + (int64_t)blockIdx.x * a.gnodes;
   }
-  for (int j = lane; j < cnt; j += 32) { conn[j] = 0; in1[j] = 0; }
+  for (int j = lane; j < cnt; j += 32) {
+    g[j] = -a.dpl[start + j];
+    st[j] = S_FREE;
+    if (cv) cv[j] = (uint16_t)a.cvl[start + j];
+  }
   for (int c = lane; c < nch; c += 32) best[c] = 0;
   __syncwarp();
   const uint64_t kip = stream_key(a.seed, TAG_IP, 0, (uint32_t)S.bid);
   int64_t w1 = 0;
-  const int start = S.start;
+  const int B = 1 + cnt / 1024;  // nodes per growing step
+  int32_t *batch = a.gbatch + (int64_t)blockIdx.x * a.batch_cap;
   while (w1 < S.T1) {
-    unsigned long long b = 0;
-    for (int c = lane; c < nch; c += 32) b = best[c] > b ? best[c] : b;
-    b = warp_max(b);
-    int j;
-    if (b != 0) {
-      j = (int)(0xFFFFFFFFu - (unsigned)(b & 0xFFFFFFFFull));
-      if (w1 + a.cvl[start + j] > S.L1) {  // cannot fit now, nor later: retire it
-        if (lane == 0) in1[j] = 2;
-        __syncwarp();
-        rescan_chunk(j / kChunkNodes, cnt, start, conn, in1, a.dpl, best);
-        continue;
+    // extract up to B nodes in (gain desc, id asc) order; gains stay frozen until the step ends
+    int nb = 0;
+    while (nb < B && w1 < S.T1) {
+      unsigned long long b = 0;
+      for (int c = lane; c < nch; c += 32) b = best[c] > b ? best[c] : b;
+      b = warp_max(b);
+      if (b == 0) break;
+      const int j = (int)(0xFFFFFFFFu - (unsigned)(b & 0xFFFFFFFFull));
+      const int cj = cv ? (int)cv[j] : a.cvl[start + j];
+      const bool fit = w1 + cj <= S.L1;
+      if (lane == 0) {
+        st[j] = fit ? S_ONE : S_OUT;  // S_OUT: cannot fit now, nor later
+        if (fit) batch[nb] = j;
+        if (a.trace && !fit) atomicAdd(a.trace + 2, 1ull);
       }
-    } else {
+      if (fit) { nb++; w1 += cj; }
+      __syncwarp();
+      rescan_chunk(j / kChunkNodes, cnt, g, st, best);
+    }
+    if (a.trace && lane == 0) atomicAdd(a.trace + 0, 1ull);
+    if (nb == 0) {  // no frontier node fits: the smallest-hash node that fits
+      if (a.trace && lane == 0) atomicAdd(a.trace + 1, 1ull);
       unsigned long long m = ~0ull;
       for (int jj = lane; jj < cnt; jj += 32) {
-        if (in1[jj] != 0 || conn[jj] != 0 || w1 + a.cvl[start + jj] > S.L1) continue;
+        if (st[jj] != S_FREE) continue;
+        const int cjj = cv ? (int)cv[jj] : a.cvl[start + jj];
+        if (w1 + cjj > S.L1) continue;
         const unsigned long long key =
             ((unsigned long long)h32(kip, (uint32_t)a.vtx[start + jj], (uint32_t)t) << 32) | (unsigned)jj;
         m = key < m ? key : m;
       }
       m = warp_min(m);
       if (m == ~0ull) break;
-      j = (int)(unsigned)(m & 0xFFFFFFFFull);
-    }
-    w1 += a.cvl[start + j];
-    if (lane == 0) in1[j] = 1;
-    __syncwarp();
-    const int v = a.vtx[start + j];
-    for (int e = a.xadj[v] + lane; e < a.xadj[v + 1]; e += 32) {
-      const int u = a.adjncy[e];
-      const int2 sl = a.splo[u];
-      if (sl.x != si || in1[sl.y] != 0) continue;
-      const int nc = conn[sl.y] + a.adjwgt[e];
-      conn[sl.y] = nc;
-      atomicMax(&best[sl.y / kChunkNodes], gain_key(2 * (int64_t)nc - a.dpv[u], sl.y));
+      const int j = (int)(unsigned)(m & 0xFFFFFFFFull);
+      w1 += cv ? (int)cv[j] : a.cvl[start + j];
+      if (lane == 0) { st[j] = S_ONE; batch[0] = j; }
+      nb = 1;
+      __syncwarp();
     }
     __syncwarp();
-    rescan_chunk(j / kChunkNodes, cnt, start, conn, in1, a.dpl, best);
+    // neighbours of the step's nodes, over their concatenated local rows (32 nodes at a time)
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+      int rs = 0, d = 0;
+      if (b0 + lane < nb) {
+        const int p = start + batch[b0 + lane];
+        rs = a.lxadj[p];
+        d = a.lxadj[p + 1] - rs;
+      }
+      int incl = d;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int excl = incl - d, total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      for (int f0 = 0; f0 < total; f0 += 32) {
+        const int f = f0 + lane;
+        int q = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int val = __shfl_sync(0xFFFFFFFFu, incl, q + step - 1);
+          if (val <= f) q += step;
+        }
+        const int sq = __shfl_sync(0xFFFFFFFFu, rs, q), eq = __shfl_sync(0xFFFFFFFFu, excl, q);
+        if (f < total) {
+          const int2 e = a.ladj[sq + (f - eq)];
+          const uint8_t su = st[e.x];
+          if (su == S_FREE || su == S_FRONT) {
+            const int ng = atomicAdd(&g[e.x], 2 * e.y) + 2 * e.y;
+            if (su == S_FREE) st[e.x] = S_FRONT;
+            atomicMax(&best[e.x / kChunkNodes], gain_key(ng, e.x));
+          }
+        }
+      }
+    }
+    __syncwarp();
   }
   // cut of this trial inside the subproblem
   unsigned long long cut = 0;
   for (int jj = lane; jj < cnt; jj += 32) {
-    if (in1[jj] != 1) continue;
-    const int v = a.vtx[start + jj];
-    for (int e = a.xadj[v]; e < a.xadj[v + 1]; e++) {
-      const int2 sl = a.splo[a.adjncy[e]];
-      if (sl.x == si && in1[sl.y] != 1) cut += (unsigned long long)a.adjwgt[e];
+    if (st[jj] != S_ONE) continue;
+    const int p = start + jj;
+    for (int e = a.lxadj[p]; e < a.lxadj[p + 1]; e++) {
+      const int2 x = a.ladj[e];
+      if (st[x.x] != S_ONE) cut += (unsigned long long)x.y;
     }
   }
   cut = warp_sum(cut);
   if (lane == 0) a.trial_cut[blockIdx.x] = (int64_t)cut;
   uint8_t *fl = a.flags + (int64_t)t * a.n + start;
-  for (int jj = lane; jj < cnt; jj += 32) fl[jj] = in1[jj] == 1;
+  for (int jj = lane; jj < cnt; jj += 32) fl[jj] = st[jj] == S_ONE;
 }
 
 __global__ void k_sub_count(const int32_t *sp, const int32_t *vwgt, int n, int32_t *cnt, long long *w) {
@@ -189,20 +247,44 @@ __global__ void k_sub_lists(const uint64_t *keys, int n, int live, const int32_t
   }
 }
 
-// deg'(v): weight to nodes of the same subproblem, one warp per listed node
+// deg'(v) (weight to nodes of the same subproblem) and the number of such
+// neighbours, one warp per listed node
 __global__ void k_sub_dp(const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *vtx,
-                         const int2 *splo, int live, int32_t *dpl, int32_t *dpv) {
+                         const int2 *splo, int live, int32_t *dpl, int32_t *lcnt) {
   const int lane = (int)lane_id();
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int p = wid; p < live; p += nw) {
     const int v = vtx[p];
     const int s = splo[v].x;
-    int sum = 0;
+    int sum = 0, c = 0;
     for (int e = xadj[v] + lane; e < xadj[v + 1]; e += 32)
-      if (splo[adjncy[e]].x == s) sum += adjwgt[e];
+      if (splo[adjncy[e]].x == s) { sum += adjwgt[e]; c++; }
     sum = warp_sum(sum);
-    if (lane == 0) { dpl[p] = sum; dpv[v] = sum; }
+    c = warp_sum(c);
+    if (lane == 0) { dpl[p] = sum; lcnt[p] = c; }
+  }
+}
+
+// local rows: (local index, weight) of the internal neighbours of every listed node
+__global__ void k_sub_rows(const int32_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, const int32_t *vtx,
+                           const int2 *splo, int live, const int32_t *lxadj, int2 *ladj) {
+  const int lane = (int)lane_id();
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = wid; p < live; p += nw) {
+    const int v = vtx[p];
+    const int s = splo[v].x;
+    int pos = lxadj[p];
+    for (int e0 = xadj[v]; e0 < xadj[v + 1]; e0 += 32) {
+      const int e = e0 + lane;
+      int2 sl = make_int2(-1, 0);
+      if (e < xadj[v + 1]) sl = splo[adjncy[e]];
+      const bool in = sl.x == s;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, in);
+      if (in) ladj[pos + __popc(m & lanemask_lt())] = make_int2(sl.y, adjwgt[e]);
+      pos += __popc(m);
+    }
   }
 }
 
@@ -232,6 +314,13 @@ __global__ void k_ip_assign(int n, int live, const int32_t *vtx, const int2 *spl
   }
 }
 
+__global__ void k_max_weight(const int32_t *w, int n, int *out) {
+  int m = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = w[i] > m ? w[i] : m;
+  m = warp_max(m);
+  if (lane_id() == 0 && m) atomicMax(out, m);
+}
+
 int32_t ceil_log2(int64_t k) {
   int32_t b = 0;
   while (((int64_t)1 << b) < k) b++;
@@ -253,7 +342,9 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
   if (k <= 1 || n == 0) return;
   const int grid = grid_for(n, 256, ctx->num_sms * 8);
   DBuf<int32_t> sp(ctx, (size_t)n), vtx(ctx, (size_t)n), cvl(ctx, (size_t)n), dpl(ctx, (size_t)n),
-      dpv(ctx, (size_t)n);
+      lxadj(ctx, (size_t)n + 1);
+  DBuf<int2> ladj(ctx, (size_t)(g.m2 > 0 ? g.m2 : 1));
+  DBuf<int> maxc(ctx, 1);
   DBuf<int2> splo(ctx, (size_t)n);
   DBuf<uint64_t> keys(ctx, (size_t)n);
   DBuf<uint32_t> vals(ctx, (size_t)n);
@@ -261,6 +352,10 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
   const int64_t eps_l = eps_ppm / ceil_log2(k);
   std::vector<HostSub> subs{{k, 0, 1}};
   GP_CUDA(cudaFuncSetAttribute(k_ip_grow, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes));
+  maxc.zero();
+  k_max_weight<<<grid, 256, 0, ctx->stream>>>(g.vwgt, n, maxc.get());
+  GP_LAUNCH_CHECK();
+  const int cvmax = read_scalar(ctx, maxc.get());
   DBuf<uint8_t> flags(ctx, (size_t)trials * n);
   while (!subs.empty()) {
     const int ns = (int)subs.size();
@@ -286,7 +381,12 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
                                                 splo.get());
     GP_LAUNCH_CHECK();
     k_sub_dp<<<grid_for((int64_t)live * 32, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(
-        g.xadj, g.adjncy, g.adjwgt, vtx.get(), splo.get(), live, dpl.get(), dpv.get());
+        g.xadj, g.adjncy, g.adjwgt, vtx.get(), splo.get(), live, dpl.get(), lxadj.get());
+    GP_LAUNCH_CHECK();
+    GP_CUDA(cudaMemsetAsync(lxadj.get() + live, 0, sizeof(int32_t), ctx->stream));
+    scan_exclusive_i32(ctx, lxadj.get(), lxadj.get(), live + 1, nullptr);
+    k_sub_rows<<<grid_for((int64_t)live * 32, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+        g.xadj, g.adjncy, g.adjwgt, vtx.get(), splo.get(), live, lxadj.get(), ladj.get());
     GP_LAUNCH_CHECK();
     std::vector<Sub> hsub(ns);
     int maxcnt = 0;
@@ -306,29 +406,59 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
     const int nblocks = ns * trials;
     DBuf<int64_t> tcut(ctx, (size_t)nblocks);
     IpArgs a{};
-    a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt;
-    a.vtx = vtx.get(); a.cvl = cvl.get(); a.dpl = dpl.get(); a.splo = splo.get(); a.dpv = dpv.get();
+    a.lxadj = lxadj.get(); a.ladj = ladj.get();
+    a.vtx = vtx.get(); a.cvl = cvl.get(); a.dpl = dpl.get();
     a.subs = dsub.get(); a.trials = trials; a.n = n; a.seed = seed;
-    // shared-memory state: chunk maxima (8 B per 64 nodes) + conn (4 B) + state (1 B) per node
-    const int smem_cap = (kMaxSmemBytes - 64) * kChunkNodes / (8 + 5 * kChunkNodes);
+    a.cv16 = cvmax <= 65535 ? 1 : 0;
+    // shared-memory state: chunk maxima (8 B per 64 nodes) + gain (4 B) + weight (2 B, when it fits) +
+    // state (1 B) per node
+    const int per_node = a.cv16 ? 7 : 5;
+    const int smem_cap = (kMaxSmemBytes - 64) * kChunkNodes / (8 + per_node * kChunkNodes);
     a.smem_nodes = std::max(1, std::min(maxcnt, smem_cap));
     const size_t smem_bytes = (size_t)((a.smem_nodes + kChunkNodes - 1) / kChunkNodes) * 8 +
-                              (size_t)a.smem_nodes * 5;
-    DBuf<int32_t> gconn;
-    DBuf<uint8_t> gin;
+                              (size_t)a.smem_nodes * per_node;
+    DBuf<int32_t> gg;
+    DBuf<uint8_t> gst;
+    DBuf<uint16_t> gcv;
     DBuf<unsigned long long> gbest;
     if (maxcnt > a.smem_nodes) {
       a.gnodes = maxcnt;
       a.gchunks = (maxcnt + kChunkNodes - 1) / kChunkNodes;
-      gconn.reset(ctx, (size_t)nblocks * a.gnodes);
-      gin.reset(ctx, (size_t)nblocks * a.gnodes);
+      gg.reset(ctx, (size_t)nblocks * a.gnodes);
+      gst.reset(ctx, (size_t)nblocks * a.gnodes);
+      if (a.cv16) gcv.reset(ctx, (size_t)nblocks * a.gnodes);
       gbest.reset(ctx, (size_t)nblocks * a.gchunks);
-      a.gconn = gconn.get(); a.gin = gin.get(); a.gbest = gbest.get();
+      a.gg = gg.get(); a.gst = gst.get(); a.gcv = gcv.get(); a.gbest = gbest.get();
     }
     a.trial_cut = tcut.get();
     a.flags = flags.get();
+    a.batch_cap = 1 + maxcnt / 1024;
+    DBuf<int32_t> gbatch(ctx, (size_t)nblocks * a.batch_cap);
+    a.gbatch = gbatch.get();
+    const bool trace = getenv("GP_TRACE") != nullptr;
+    DBuf<unsigned long long> tr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (trace) {
+      tr.reset(ctx, 3);
+      tr.zero();
+      a.trace = tr.get();
+      GP_CUDA(cudaEventCreate(&e0));
+      GP_CUDA(cudaEventCreate(&e1));
+      GP_CUDA(cudaEventRecord(e0, ctx->stream));
+    }
     k_ip_grow<<<nblocks, 32, smem_bytes, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
+    if (trace) {
+      GP_CUDA(cudaEventRecord(e1, ctx->stream));
+      unsigned long long h[3];
+      read_back(ctx, tr.get(), sizeof(h), h);
+      float ms = 0;
+      GP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      fprintf(stderr, "[gp ip] subproblems=%d max_nodes=%d grow_ms=%.2f steps=%llu fallbacks=%llu retired=%llu\n",
+              ns, maxcnt, ms, h[0], h[1], h[2]);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
     DBuf<int32_t> best(ctx, (size_t)ns), child(ctx, (size_t)2 * ns);
     k_ip_select<<<grid_for(ns, 128, 1024), 128, 0, ctx->stream>>>(tcut.get(), ns, trials, best.get());
     GP_LAUNCH_CHECK();
@@ -433,7 +563,7 @@ __global__ void k_block_weights(const int32_t *blk, const int32_t *vwgt, int n, 
 }  // namespace
 
 int64_t rebalance_blocks(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t Lmax, int32_t *blocks) {
-  ProfScope ps(ctx, PROF_IP);
+  ProfScope ps(ctx, PROF_REBALANCE);
   if (g.n == 0 || k <= 1) return 0;
   DBuf<long long> bw(ctx, (size_t)k), moves(ctx, 1);
   bw.zero();

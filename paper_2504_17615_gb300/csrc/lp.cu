@@ -29,6 +29,7 @@ constexpr int kMaxKeys = 64 * kNumBuckets;
 
 struct RateArgs {
   const int32_t *xadj, *adjncy, *adjwgt, *vwgt, *label, *weight;
+  const uint8_t *label8;  // optional narrow copy of label (fewer than 256 labels) for gathers
   const int32_t *list;
   const int32_t *offs;
   int key;
@@ -54,6 +55,10 @@ __device__ __forceinline__ void add_units(unsigned long long *units, unsigned lo
     if (c) atomicAdd(units + 2, c);
     if (p) atomicAdd(units + 3, p);
   }
+}
+
+__device__ __forceinline__ int label_of(const RateArgs &a, int u) {
+  return a.label8 ? (int)a.label8[u] : a.label[u];
 }
 
 __device__ __forceinline__ unsigned slot_hash(int L, int bits) {
@@ -84,19 +89,29 @@ __device__ __forceinline__ void emit(const RateArgs &a, int i, int v, int best, 
 // candidate while reading one label weight per node in the usual case, and
 // none at all when no neighbouring label beats the node's own label.
 
-template <int MODE, int G, int U>
+// Label kinds: LK_WIDE int32 labels summed in hash tables; LK_NARROW uint8
+// labels (fewer than 256) in hash tables; LK_DENSE uint8 labels below
+// kDenseLabels summed in a dense per-group array indexed by label.
+enum LabelKind { LK_WIDE = 0, LK_NARROW = 1, LK_DENSE = 2 };
+constexpr int kDenseLabels = 128;
+
+template <int MODE, int G, int U, int LK>
 __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
   static_assert(G == 8 || G == 16 || G == 32, "group width");
   constexpr int NV = 32 / G;
   constexpr int PER = NV * U;
-  constexpr int TS = 2 * G;  // table slots per group
-  __shared__ int s_tk[kWarpsPerBlock][U * 64];
-  __shared__ int s_tv[kWarpsPerBlock][U * 64];
+  constexpr int TS = 2 * G;  // hash-table slots per group
+  constexpr int TW = LK == LK_DENSE ? U * NV * kDenseLabels : U * 64;  // table words per warp
+  __shared__ int s_tk[LK == LK_DENSE ? 1 : kWarpsPerBlock][LK == LK_DENSE ? 1 : U * 64];
+  __shared__ int s_tv[kWarpsPerBlock][TW];
   if (a.stop && *a.stop) return;
   const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane % G;
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
-  for (int t = lane; t < U * 64; t += 32) { s_tk[wib][t] = -1; s_tv[wib][t] = 0; }
+  for (int t = lane; t < TW; t += 32) {
+    if (LK != LK_DENSE) s_tk[wib][t] = -1;
+    s_tv[wib][t] = 0;
+  }
   __syncwarp();
   const int begin = a.offs[a.key], end = a.offs[a.key + 1];
   const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -115,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
       const int vv = ok ? v[q] : 0;
       st[q] = a.xadj[vv];
       deg[q] = ok ? a.xadj[vv + 1] - st[q] : 0;
-      own[q] = ok ? a.label[vv] : -2;
+      own[q] = ok ? (LK == LK_WIDE ? a.label[vv] : (int)a.label8[vv]) : -2;
       cv[q] = a.vwgt[vv];
     }
 #pragma unroll
@@ -125,46 +140,68 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
       w[q] = ok ? a.adjwgt[st[q] + gl] : 0;
     }
 #pragma unroll
-    for (int q = 0; q < U; q++) L[q] = u[q] >= 0 ? a.label[u[q]] : -1;
-    // sum equal labels per group in the shared tables
-    int slot[U];
-    bool lead[U];
-#pragma unroll
-    for (int q = 0; q < U; q++) {
-      int *tk = &s_tk[wib][q * 64 + grp * TS];
-      slot[q] = -1;
-      lead[q] = false;
-      if (u[q] >= 0) {
-        unsigned sl = ((unsigned)L[q] * 2654435761u) >> (32 - (G == 8 ? 4 : G == 16 ? 5 : 6));
-        for (int p = 0; p < TS; p++) {  // bounded: a group has at most G labels in 2G slots
-          const int prev = atomicCAS(&tk[sl], -1, L[q]);
-          if (prev == -1) { lead[q] = true; break; }
-          if (prev == L[q]) break;
-          sl = (sl + 1) & (TS - 1);
-        }
-        slot[q] = q * 64 + grp * TS + (int)sl;
-        atomicAdd(&s_tv[wib][slot[q]], w[q]);
-      }
-    }
-    __syncwarp();
-    int sum[U];
-#pragma unroll
-    for (int q = 0; q < U; q++) sum[q] = slot[q] >= 0 ? s_tv[wib][slot[q]] : 0;
-    __syncwarp();
-#pragma unroll
     for (int q = 0; q < U; q++)
-      if (lead[q]) { s_tk[wib][slot[q]] = -1; s_tv[wib][slot[q]] = 0; }
-    __syncwarp();
+      L[q] = u[q] >= 0 ? (LK == LK_WIDE ? a.label[u[q]] : (int)a.label8[u[q]]) : -1;
+    // sum equal labels per group in shared memory
+    int slot[U], own_r[U], sum[U];
+    bool lead[U];
+    if (LK == LK_DENSE) {
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        slot[q] = (q * NV + grp) * kDenseLabels;
+        if (u[q] >= 0) atomicAdd(&s_tv[wib][slot[q] + L[q]], w[q]);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        sum[q] = u[q] >= 0 ? s_tv[wib][slot[q] + L[q]] : 0;
+        own_r[q] = v[q] >= 0 ? s_tv[wib][slot[q] + own[q]] : 0;
+        lead[q] = u[q] >= 0;  // duplicates of a label are harmless below
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++)
+        if (u[q] >= 0) s_tv[wib][slot[q] + L[q]] = 0;
+      __syncwarp();
+    } else {
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        int *tk = &s_tk[wib][q * 64 + grp * TS];
+        slot[q] = -1;
+        lead[q] = false;
+        if (u[q] >= 0) {
+          unsigned sl = ((unsigned)L[q] * 2654435761u) >> (32 - (G == 8 ? 4 : G == 16 ? 5 : 6));
+          for (int p = 0; p < TS; p++) {  // bounded: a group has at most G labels in 2G slots
+            const int prev = atomicCAS(&tk[sl], -1, L[q]);
+            if (prev == -1) { lead[q] = true; break; }
+            if (prev == L[q]) break;
+            sl = (sl + 1) & (TS - 1);
+          }
+          slot[q] = q * 64 + grp * TS + (int)sl;
+          atomicAdd(&s_tv[wib][slot[q]], w[q]);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++) sum[q] = slot[q] >= 0 ? s_tv[wib][slot[q]] : 0;
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++)
+        if (lead[q]) { s_tk[wib][slot[q]] = -1; s_tv[wib][slot[q]] = 0; }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++)
+        own_r[q] = __reduce_max_sync(gmask, (lead[q] && L[q] == own[q]) ? sum[q] : 0);
+    }
 #pragma unroll
     for (int q = 0; q < U; q++) {
-      const int own_r = __reduce_max_sync(gmask, (lead[q] && L[q] == own[q]) ? sum[q] : 0);
       bool alive = lead[q] && L[q] != own[q];
       uc += alive;
       unsigned best = 0xFFFFFFFFu;
       bool searching = v[q] >= 0;
       while (__any_sync(FULL, searching)) {
         const int r = __reduce_max_sync(gmask, (searching && alive) ? sum[q] : -1);
-        if (r < 0 || (MODE == RATE_LP && r <= own_r)) searching = false;
+        if (r < 0 || (MODE == RATE_LP && r <= own_r[q])) searching = false;
         const bool top = searching && alive && sum[q] == r;
         const unsigned h = top ? h32(a.ktie, (uint32_t)v[q], (uint32_t)L[q]) : 0xFFFFFFFFu;
         const unsigned hmin = __reduce_min_sync(gmask, h);
@@ -210,10 +247,10 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
     const int v = a.list[i];
     const int start = a.xadj[v];
     const int deg = a.xadj[v + 1] - start;
-    const int own = a.label[v];
+    const int own = label_of(a, v);
     const int cv = a.vwgt[v];
     for (int j = lane; j < deg; j += 32) {
-      const int L = a.label[a.adjncy[start + j]];
+      const int L = label_of(a, a.adjncy[start + j]);
       const int w = a.adjwgt[start + j];
       unsigned s = slot_hash(L, 8);
       for (int probe = 0; probe < kMedSlots; probe++) {  // bounded: the table never fills
@@ -295,7 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
     const int v = a.list[i];
     const int start = a.xadj[v];
     const int deg = a.xadj[v + 1] - start;
-    const int own = a.label[v];
+    const int own = label_of(a, v);
     const int cv = a.vwgt[v];
     int bits = 1;
     while ((1 << bits) < 2 * deg) bits++;
@@ -304,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
     int *tk = in_smem ? s_k : gk;
     int *tv = in_smem ? s_v : gv;
     for (int j = threadIdx.x; j < deg; j += blockDim.x) {
-      const int L = a.label[a.adjncy[start + j]];
+      const int L = label_of(a, a.adjncy[start + j]);
       const int w = a.adjwgt[start + j];
       unsigned s = slot_hash(L, bits);
       for (int probe = 0; probe < tsize; probe++) {  // bounded: the table never fills
@@ -436,41 +473,70 @@ __global__ void __launch_bounds__(kThreads) k_bucket_scatter(BucketArgs b, int n
 
 struct Counters {
   int stop;
-  int nov;
+  int nov;   // proposers of overflowing targets this sub-round
+  int nmov;  // proposers accepted outright this sub-round
+  int pad0;
   long long moved_sub;
   long long moved_round;
   long long moved_total;
   long long emptied;
   long long nclusters;
-  long long pad;
 };
 
+// Every active node's proposal is read once: the node's slot in `target` is
+// reset, and the proposal goes to the list of outright acceptances (the
+// target's snapshot weight plus all incoming weight fits) or to the list of
+// proposers of overflowing targets.  Slots in both lists are reserved once
+// per block and iteration.
 __global__ void __launch_bounds__(kThreads) k_decide(const int32_t *list, const int32_t *offs,
-                                                     int k0, int k1, const int32_t *target,
-                                                     const int32_t *vwgt, const int32_t *weight,
-                                                     const int32_t *incoming, int64_t bound,
-                                                     uint8_t *acc, uint64_t *ov_key,
-                                                     uint32_t *ov_val, Counters *cnt, uint64_t kprio) {
+                                                     int k0, int k1, int32_t *target,
+                                                     const int32_t *weight, const int32_t *incoming,
+                                                     int64_t bound, int32_t *mov_v, int32_t *mov_k,
+                                                     uint64_t *ov_key, uint32_t *ov_val, Counters *cnt,
+                                                     uint64_t kprio) {
+  __shared__ int s_a[kWarpsPerBlock + 1], s_o[kWarpsPerBlock + 1];
   if (cnt->stop) return;
   const int begin = offs[k0], end = offs[k1];
   const int stride = gridDim.x * blockDim.x;
+  const int lane = (int)lane_id(), w = threadIdx.x >> 5;
   for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += stride) {
     const int i = base + (int)threadIdx.x;
-    bool over = false;
-    int v = 0, K = 0;
+    bool acc = false, over = false;
+    int v = 0, K = -1;
     if (i < end) {
       v = list[i];
       K = target[v];
       if (K >= 0) {
-        if ((int64_t)weight[K] + incoming[K] <= bound) acc[v] = 1;
+        target[v] = -1;
+        if ((int64_t)weight[K] + incoming[K] <= bound) acc = true;
         else over = true;
       }
     }
-    const int pos = warp_append(&cnt->nov, over);
+    const unsigned ma = __ballot_sync(0xFFFFFFFFu, acc), mo = __ballot_sync(0xFFFFFFFFu, over);
+    if (lane == 0) { s_a[w] = __popc(ma); s_o[w] = __popc(mo); }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ra = 0, ro = 0;
+      for (int j = 0; j < kWarpsPerBlock; j++) {
+        const int ca = s_a[j], co = s_o[j];
+        s_a[j] = ra; s_o[j] = ro;
+        ra += ca; ro += co;
+      }
+      s_a[kWarpsPerBlock] = ra ? atomicAdd(&cnt->nmov, ra) : 0;
+      s_o[kWarpsPerBlock] = ro ? atomicAdd(&cnt->nov, ro) : 0;
+    }
+    __syncthreads();
+    if (acc) {
+      const int pos = s_a[kWarpsPerBlock] + s_a[w] + __popc(ma & lanemask_lt());
+      mov_v[pos] = v;
+      mov_k[pos] = K;
+    }
     if (over) {
+      const int pos = s_o[kWarpsPerBlock] + s_o[w] + __popc(mo & lanemask_lt());
       ov_key[pos] = ((uint64_t)(uint32_t)K << 32) | h32(kprio, (uint32_t)v, 0);
       ov_val[pos] = (uint32_t)v;
     }
+    __syncthreads();
   }
 }
 
@@ -495,8 +561,10 @@ __global__ void k_ov_weights(const uint32_t *vals, int n, const int32_t *vwgt, i
     cs[i] = vwgt[vals[i]];
 }
 
+// Sorted by (target, prio, node): accept while the running weight within the
+// target's segment fits (ps = exclusive prefix sum of the weights).
 __global__ void k_ov_accept(const uint64_t *keys, const uint32_t *vals, int n, const int64_t *ps,
-                            const int32_t *vwgt, const int32_t *weight, int64_t bound, uint8_t *acc) {
+                            const int32_t *vwgt, const int32_t *weight, int64_t bound, uint8_t *ov_acc) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
     const uint64_t seg = k & 0xFFFFFFFF00000000ull;
@@ -507,80 +575,94 @@ __global__ void k_ov_accept(const uint64_t *keys, const uint32_t *vals, int n, c
     }
     const int K = (int)(k >> 32);
     const int64_t incl = ps[i] - ps[lo] + vwgt[vals[i]];
-    acc[vals[i]] = (int64_t)weight[K] + incl <= bound ? 1 : 0;
+    ov_acc[i] = (int64_t)weight[K] + incl <= bound ? 1 : 0;
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_apply(const int32_t *list, const int32_t *offs, int k0,
-                                                    int k1, const int32_t *target, uint8_t *acc,
-                                                    const int32_t *vwgt, int32_t *label,
-                                                    int32_t *weight, int32_t *size,
-                                                    int32_t *leave_cnt, int32_t *first_own,
-                                                    Counters *cnt, int agg_weights) {
-  if (cnt->stop) return;
-  const int begin = offs[k0], end = offs[k1];
-  const int stride = gridDim.x * blockDim.x;
+struct ApplyArgs {
+  const int32_t *mov_v, *mov_k;
+  const uint64_t *ov_key;
+  const uint32_t *ov_val;
+  const uint8_t *ov_acc;
+  int nmov, nov;
+  const int32_t *vwgt;
+  int32_t *label, *weight, *size, *leave_cnt, *incoming;
+  uint8_t *label8;
+  int32_t *own;      // per proposer: the label it left (first leavers only)
+  uint8_t *first;    // per proposer: first to leave its label this sub-round
+  int nshared;       // > 0: few labels; weight changes summed per block in shared memory
+  Counters *cnt;
+};
+
+__device__ __forceinline__ void proposal(const ApplyArgs &a, int t, int &v, int &K, bool &mv) {
+  if (t < a.nmov) {
+    v = a.mov_v[t]; K = a.mov_k[t]; mv = true;
+  } else {
+    const int j = t - a.nmov;
+    v = (int)a.ov_val[j]; K = (int)(a.ov_key[j] >> 32); mv = a.ov_acc[j] != 0;
+  }
+}
+
+// Moves every accepted proposer (outright or through the overflow order).
+__global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
+  extern __shared__ int s_dw[];
+  for (int t = threadIdx.x; t < a.nshared; t += blockDim.x) s_dw[t] = 0;
+  if (a.nshared) __syncthreads();
+  const int total = a.nmov + a.nov;
   long long moved = 0;
-  for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += stride) {
-    const int i = base + (int)threadIdx.x;
-    bool mv = false;
-    int v = 0, K = 0, own = 0, c = 0;
-    if (i < end) {
-      v = list[i];
-      K = target[v];
-      mv = K >= 0 && acc[v] == 1;
-      if (mv) {
-        own = label[v];
-        c = vwgt[v];
-        label[v] = K;
-        if (size) {
-          atomicAdd(&size[K], 1);
-          atomicSub(&size[own], 1);
-          if (atomicAdd(&leave_cnt[own], 1) == 0) {
-            acc[v] = 2;
-            first_own[v] = own;
-          }
-        }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int v, K;
+    bool mv;
+    proposal(a, t, v, K, mv);
+    uint8_t first = 0;
+    if (mv) {
+      const int own = a.label[v], c = a.vwgt[v];
+      a.label[v] = K;
+      if (a.label8) a.label8[v] = (uint8_t)K;
+      if (a.size) {
+        atomicAdd(&a.size[K], 1);
+        atomicSub(&a.size[own], 1);
+        if (atomicAdd(&a.leave_cnt[own], 1) == 0) { first = 1; a.own[t] = own; }
       }
+      if (a.nshared) {
+        atomicAdd(&s_dw[K], c);
+        atomicSub(&s_dw[own], c);
+      } else {
+        atomicAdd(&a.weight[K], c);
+        atomicSub(&a.weight[own], c);
+      }
+      moved++;
     }
-    if (agg_weights) {
-      warp_agg_add(weight, K, c, mv);
-      warp_agg_add(weight, own, -c, mv);
-    } else if (mv) {
-      atomicAdd(&weight[K], c);
-      atomicSub(&weight[own], c);
-    }
-    moved += mv;
+    if (a.size) a.first[t] = first;
+  }
+  if (a.nshared) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < a.nshared; t += blockDim.x)
+      if (s_dw[t]) atomicAdd(&a.weight[t], s_dw[t]);
   }
   moved = warp_sum(moved);
   if (lane_id() == 0 && moved)
-    atomicAdd((unsigned long long *)&cnt->moved_sub, (unsigned long long)moved);
+    atomicAdd((unsigned long long *)&a.cnt->moved_sub, (unsigned long long)moved);
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(const int32_t *list, const int32_t *offs,
-                                                       int k0, int k1, int32_t *target,
-                                                       uint8_t *acc, int32_t *incoming,
-                                                       const int32_t *size, int32_t *leave_cnt,
-                                                       const int32_t *first_own, Counters *cnt) {
-  if (cnt->stop) return;
-  const int begin = offs[k0], end = offs[k1];
+// Clears the incoming weights, counts the clusters the moves emptied.
+__global__ void __launch_bounds__(kThreads) k_finalize(ApplyArgs a) {
+  const int total = a.nmov + a.nov;
   long long emptied = 0;
-  for (int i = begin + blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
-    const int v = list[i];
-    const int K = target[v];
-    if (K < 0) continue;
-    incoming[K] = 0;
-    if (acc[v] == 2) {
-      const int own = first_own[v];
-      if (size[own] == 0) emptied++;
-      leave_cnt[own] = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int v, K;
+    bool mv;
+    proposal(a, t, v, K, mv);
+    a.incoming[K] = 0;
+    if (a.size && a.first[t]) {
+      const int own = a.own[t];
+      if (a.size[own] == 0) emptied++;
+      a.leave_cnt[own] = 0;
     }
-    target[v] = -1;
-    acc[v] = 0;
   }
   emptied = warp_sum(emptied);
   if (lane_id() == 0 && emptied)
-    atomicAdd((unsigned long long *)&cnt->emptied, (unsigned long long)emptied);
+    atomicAdd((unsigned long long *)&a.cnt->emptied, (unsigned long long)emptied);
 }
 
 __global__ void k_subround_end(Counters *cnt, int count_clusters, long long n_min) {
@@ -600,11 +682,11 @@ __global__ void k_round_end(Counters *cnt) {
 }
 
 __global__ void k_counters_init(Counters *cnt, long long nclusters) {
-  cnt->stop = 0; cnt->nov = 0; cnt->moved_sub = 0; cnt->moved_round = 0; cnt->moved_total = 0;
-  cnt->emptied = 0; cnt->nclusters = nclusters; cnt->pad = 0;
+  cnt->stop = 0; cnt->nov = 0; cnt->nmov = 0; cnt->pad0 = 0; cnt->moved_sub = 0; cnt->moved_round = 0;
+  cnt->moved_total = 0; cnt->emptied = 0; cnt->nclusters = nclusters;
 }
 
-__global__ void k_reset_nov(Counters *cnt) { cnt->nov = 0; }
+__global__ void k_reset_lists(Counters *cnt) { cnt->nov = 0; cnt->nmov = 0; }
 
 __global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -650,18 +732,29 @@ void make_tables(gp_ctx *ctx, const DevGraph &g, RateTables &t) {
   }
 }
 
-template <int MODE>
-void launch_rate(gp_ctx *ctx, RateArgs a, int bucket_key_base, const RateTables &t) {
+template <int MODE, int LK>
+void launch_groups(gp_ctx *ctx, const RateArgs &a0, int bucket_key_base) {
   const int grid_w = ctx->num_sms * 8;
+  RateArgs a = a0;
   a.key = bucket_key_base + 0;
-  k_rate_group<MODE, 8, 2><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  k_rate_group<MODE, 8, 2, LK><<<grid_w, kThreads, 0, ctx->stream>>>(a);
   GP_LAUNCH_CHECK();
   a.key = bucket_key_base + 1;
-  k_rate_group<MODE, 16, 2><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  k_rate_group<MODE, 16, 2, LK><<<grid_w, kThreads, 0, ctx->stream>>>(a);
   GP_LAUNCH_CHECK();
   a.key = bucket_key_base + 2;
-  k_rate_group<MODE, 32, 4><<<grid_w, kThreads, 0, ctx->stream>>>(a);
+  k_rate_group<MODE, 32, 4, LK><<<grid_w, kThreads, 0, ctx->stream>>>(a);
   GP_LAUNCH_CHECK();
+}
+
+// nlabels: number of labels (chooses the narrow / dense group kernels when
+// a uint8 copy of the labels is present)
+template <int MODE>
+void launch_rate(gp_ctx *ctx, RateArgs a, int bucket_key_base, const RateTables &t, int64_t nlabels) {
+  const int grid_w = ctx->num_sms * 8;
+  if (MODE == RATE_LP && a.label8 && nlabels <= kDenseLabels) launch_groups<MODE, LK_DENSE>(ctx, a, bucket_key_base);
+  else if (MODE == RATE_LP && a.label8) launch_groups<MODE, LK_NARROW>(ctx, a, bucket_key_base);
+  else launch_groups<MODE, LK_WIDE>(ctx, a, bucket_key_base);
   a.key = bucket_key_base + 3;
   k_rate_medium<MODE><<<grid_w, kThreads, 0, ctx->stream>>>(a);
   GP_LAUNCH_CHECK();
@@ -682,28 +775,31 @@ int bits_for(int64_t x) {
 }
 
 LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int32_t *size,
-                int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev) {
+                int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev,
+                uint8_t *label8) {
   LpResult res;
   const int n = g.n;
   const int S = p.subrounds;
   GP_REQUIRE(S >= 1 && S <= 64, GP_ERR_INVALID, "lp_subrounds must be in [1, 64]");
   const int nkeys = S * kNumBuckets;
   DBuf<int32_t> list(ctx, (size_t)n), target(ctx, (size_t)n), incoming(ctx, (size_t)nlabels);
-  DBuf<uint8_t> acc(ctx, (size_t)n);
   DBuf<int32_t> cnt(ctx, (size_t)nkeys), offs(ctx, (size_t)nkeys + 1), cursor(ctx, (size_t)nkeys);
+  DBuf<int32_t> mov_v(ctx, (size_t)n), mov_k(ctx, (size_t)n);
   DBuf<uint64_t> ov_key(ctx, (size_t)n);
   DBuf<uint32_t> ov_val(ctx, (size_t)n);
-  DBuf<int32_t> leave_cnt, first_own;
+  DBuf<uint8_t> ov_acc(ctx, (size_t)n);
+  DBuf<int32_t> leave_cnt, own_of;
+  DBuf<uint8_t> first;
   if (size) {
     leave_cnt.reset(ctx, (size_t)nlabels);
     leave_cnt.zero();
-    first_own.reset(ctx, (size_t)n);
+    own_of.reset(ctx, (size_t)n);
+    first.reset(ctx, (size_t)n);
   }
   DBuf<Counters> counters(ctx, 1);
   Counters *C = counters.get();
   k_fill_i32<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(target.get(), n, -1);
   GP_LAUNCH_CHECK();
-  acc.zero();
   incoming.zero();
   int64_t ncl0 = 0;
   if (p.count_clusters && nclusters_dev) read_back(ctx, nclusters_dev, sizeof(int64_t), &ncl0);
@@ -713,6 +809,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   make_tables(ctx, g, tables);
   unsigned long long *units_rate = ctx->d_units ? ctx->d_units + p.prof_rate * PROF_UNITS : nullptr;
 
+  TraceTimer trace(ctx);
   const int grid = ctx->num_sms * 8;
   const bool agg = nlabels <= 4096;  // refinement: few labels, aggregate weight updates
   bool stop = n == 0 || (p.count_clusters && ncl0 <= p.n_min);
@@ -739,29 +836,31 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
       a.label = label; a.weight = weight; a.list = list.get(); a.offs = offs.get();
       a.bound = p.bound; a.ktie = ktie; a.target = target.get(); a.incoming = incoming.get();
-      a.stop = &C->stop; a.units = units_rate;
+      a.stop = &C->stop; a.units = units_rate; a.label8 = label8;
       {
         ProfScope ps(ctx, p.prof_rate);
-        launch_rate<RATE_LP>(ctx, a, s * kNumBuckets, tables);
+        launch_rate<RATE_LP>(ctx, a, s * kNumBuckets, tables, nlabels);
       }
       const int k0 = s * kNumBuckets, k1 = s * kNumBuckets + kNumBuckets;
-      int nov = 0;
       {
         ProfScope ps(ctx, p.prof_accept);
-        k_reset_nov<<<1, 1, 0, ctx->stream>>>(C);
+        k_reset_lists<<<1, 1, 0, ctx->stream>>>(C);
         GP_LAUNCH_CHECK();
-        k_decide<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(),
-                                                      g.vwgt, weight, incoming.get(), p.bound,
-                                                      acc.get(), ov_key.get(), ov_val.get(), C, kprio);
+        k_decide<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(), weight,
+                                                      incoming.get(), p.bound, mov_v.get(), mov_k.get(),
+                                                      ov_key.get(), ov_val.get(), C, kprio);
         GP_LAUNCH_CHECK();
       }
-      int hdr[2];
+      int hdr[3];
       read_back(ctx, C, sizeof(hdr), hdr);
       if (hdr[0]) { stop = true; break; }
-      nov = hdr[1];
+      const int nov = hdr[1], nmov = hdr[2];
       subs++;
+      res.overflow_total += nov;
+      if (nov > res.overflow_max) res.overflow_max = nov;
+      res.proposals += nov + nmov;
       if (nov > 0) {
-        ProfScope ps(ctx, p.prof_accept);
+        ProfScope ps(ctx, p.prof_overflow);
         const int kbits = bits_for(nlabels) + 32;
         radix_sort_pairs(ctx, ov_key.get(), ov_val.get(), nov, kbits);
         const int gsmall = grid_for(nov, 256, grid);
@@ -772,19 +871,24 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         GP_LAUNCH_CHECK();
         scan_exclusive_i64(ctx, cs.get(), cs.get(), nov, nullptr);
         k_ov_accept<<<gsmall, 256, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov, cs.get(), g.vwgt,
-                                                     weight, p.bound, acc.get());
+                                                     weight, p.bound, ov_acc.get());
         GP_LAUNCH_CHECK();
       }
       {
-        ProfScope ps(ctx, p.prof_accept);
-        k_apply<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(),
-                                                     acc.get(), g.vwgt, label, weight, size,
-                                                     leave_cnt.get(), first_own.get(), C, agg ? 1 : 0);
-        GP_LAUNCH_CHECK();
-        k_finalize<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(),
-                                                        acc.get(), incoming.get(), size,
-                                                        leave_cnt.get(), first_own.get(), C);
-        GP_LAUNCH_CHECK();
+        ProfScope ps(ctx, p.prof_apply);
+        ApplyArgs aa{};
+        aa.mov_v = mov_v.get(); aa.mov_k = mov_k.get(); aa.ov_key = ov_key.get(); aa.ov_val = ov_val.get();
+        aa.ov_acc = ov_acc.get(); aa.nmov = nmov; aa.nov = nov; aa.vwgt = g.vwgt; aa.label = label;
+        aa.weight = weight; aa.size = size; aa.leave_cnt = leave_cnt.get(); aa.incoming = incoming.get();
+        aa.label8 = label8; aa.own = own_of.get(); aa.first = first.get();
+        aa.nshared = agg ? (int)nlabels : 0; aa.cnt = C;
+        const int ga = grid_for((int64_t)nmov + nov, kThreads, grid);
+        if (nmov + nov > 0) {
+          k_apply<<<ga, kThreads, sizeof(int) * aa.nshared, ctx->stream>>>(aa);
+          GP_LAUNCH_CHECK();
+          k_finalize<<<ga, kThreads, 0, ctx->stream>>>(aa);
+          GP_LAUNCH_CHECK();
+        }
         k_subround_end<<<1, 1, 0, ctx->stream>>>(C, p.count_clusters ? 1 : 0, (long long)p.n_min);
         GP_LAUNCH_CHECK();
       }
@@ -798,6 +902,13 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   res.subrounds = subs;
   res.moves = hc.moved_total;
   res.nclusters = hc.nclusters;
+  if (trace.on())
+    fprintf(stderr,
+            "[gp lp] %s level=%d n=%d m2=%lld labels=%lld subrounds=%d moves=%lld proposals=%lld "
+            "overflow_total=%lld overflow_max=%lld ms=%.2f\n",
+            p.count_clusters ? "cluster" : "refine", p.level, n, (long long)g.m2, (long long)nlabels, subs,
+            (long long)res.moves, (long long)res.proposals, (long long)res.overflow_total,
+            (long long)res.overflow_max, trace.ms());
   if (p.count_clusters && nclusters_dev)
     GP_CUDA(cudaMemcpyAsync(nclusters_dev, &C->nclusters, sizeof(int64_t), cudaMemcpyDeviceToDevice,
                             ctx->stream));
@@ -843,7 +954,7 @@ void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, c
   a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
   a.label = label; a.weight = nullptr; a.list = list.get(); a.offs = offs.get();
   a.bound = U; a.ktie = kfav; a.fav_keys = keys.get(); a.stop = nullptr;
-  launch_rate<RATE_FAV>(ctx, a, 0, tables);
+  launch_rate<RATE_FAV>(ctx, a, 0, tables, 0);
 }
 
 }  // namespace gp

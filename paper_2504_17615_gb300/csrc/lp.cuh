@@ -25,21 +25,27 @@ struct LpParams {
   bool count_clusters;
   int64_t n_min;
   int32_t dbg_max_subrounds;
-  int prof_rate, prof_accept;
+  int prof_rate, prof_accept, prof_overflow, prof_apply;
 };
 
 struct LpResult {
   int32_t subrounds = 0;
   int64_t moves = 0;
   int64_t nclusters = 0;
+  int64_t proposals = 0;       // over all sub-rounds
+  int64_t overflow_total = 0;  // proposers of overflowing targets, over all sub-rounds
+  int64_t overflow_max = 0;    // largest such set in one sub-round
 };
 
 // Runs LP on g.  label (n) and weight (nlabels) are updated in place; size
 // (nlabels) is maintained when p.count_clusters (may be null otherwise).
 // nclusters_dev: device int64 with the current number of non-empty clusters
 // (clustering only).
+// label8 (may be null): a uint8 copy of label, used for the gathers and kept
+// in step (fewer than 256 labels).
 LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int32_t *size,
-                int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev);
+                int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev,
+                uint8_t *label8 = nullptr);
 
 // 2-hop favourites (Sec. 4.1): for every light singleton (deg > 0, alone in
 // its cluster, 2 c <= U), the adjacent cluster K != label(v) of largest

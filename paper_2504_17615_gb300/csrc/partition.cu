@@ -97,8 +97,9 @@ __global__ void k_project(int n, const int32_t *cmap, const int32_t *coarse, int
     fine[v] = coarse[cmap[v]];
 }
 
+template <typename B>
 __global__ void __launch_bounds__(256) k_cut(const int32_t *xadj, const int32_t *adjncy,
-                                             const int32_t *adjwgt, const int32_t *blk, int n, int64_t m2,
+                                             const int32_t *adjwgt, const B *blk, int n, int64_t m2,
                                              unsigned long long *cut) {
   const int lane = (int)lane_id();
   const int64_t chunk = 1024;
@@ -139,6 +140,12 @@ __global__ void k_bweights_global(const int32_t *blk, const int32_t *vwgt, int n
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
     atomicAdd(&bw[blk[v]], (unsigned long long)vwgt[v]);
+}
+
+// narrow copy of block ids (fewer than 256 blocks): a quarter of the bytes to gather
+__global__ void k_narrow(const int32_t *a, int64_t n, uint8_t *b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (uint8_t)a[i];
 }
 
 __global__ void k_to_i32(const unsigned long long *a, int k, int32_t *b) {
@@ -213,9 +220,17 @@ void cut_and_weights(gp_ctx *ctx, const DevGraph &g, const int32_t *blocks, int3
   DBuf<unsigned long long> c(ctx, 1);
   c.zero();
   if (g.m2 > 0) {
-    k_cut<<<grid_for((g.m2 + 1023) / 1024 * 32, 256, ctx->num_sms * 16), 256, 0, ctx->stream>>>(
-        g.xadj, g.adjncy, g.adjwgt, blocks, g.n, g.m2, c.get());
-    GP_LAUNCH_CHECK();
+    const int grid = grid_for((g.m2 + 1023) / 1024 * 32, 256, ctx->num_sms * 16);
+    if (k <= 255) {
+      DBuf<uint8_t> b8(ctx, (size_t)g.n);
+      k_narrow<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(blocks, g.n, b8.get());
+      GP_LAUNCH_CHECK();
+      k_cut<uint8_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, b8.get(), g.n, g.m2, c.get());
+      GP_LAUNCH_CHECK();
+    } else {
+      k_cut<int32_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, blocks, g.n, g.m2, c.get());
+      GP_LAUNCH_CHECK();
+    }
   }
   if (bw_host) {
     DBuf<unsigned long long> bw(ctx, (size_t)k);
@@ -238,7 +253,14 @@ int64_t refine_blocks(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t Lmax, i
   p.level = level; p.rounds = cfg.ref_rounds; p.subrounds = cfg.lp_subrounds;
   p.bound = Lmax; p.count_clusters = false; p.n_min = 0; p.dbg_max_subrounds = -1;
   p.prof_rate = PROF_REF_RATE; p.prof_accept = PROF_REF_ACCEPT;
-  LpResult r = lp_run(ctx, g, blocks, bw.get(), nullptr, k, seed, p, nullptr);
+  p.prof_overflow = PROF_REF_OVERFLOW; p.prof_apply = PROF_REF_APPLY;
+  DBuf<uint8_t> b8;
+  if (k <= 255) {
+    b8.reset(ctx, (size_t)g.n);
+    k_narrow<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(blocks, g.n, b8.get());
+    GP_LAUNCH_CHECK();
+  }
+  LpResult r = lp_run(ctx, g, blocks, bw.get(), nullptr, k, seed, p, nullptr, b8.get());
   return r.moves;
 }
 

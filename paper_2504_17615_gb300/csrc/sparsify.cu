@@ -164,6 +164,7 @@ int32_t radix_select_desc(gp_ctx *ctx, const int32_t *w, int64_t m2, int64_t R, 
 void sparsify_graph(gp_ctx *ctx, const DevGraph &g, int64_t m_hat, int32_t level, uint64_t seed,
                     int mode, DevGraph &out, gp_level_stats *st) {
   ProfScope ps(ctx, PROF_SPARSIFY);
+  TraceTimer trace(ctx);
   GP_REQUIRE(mode == GP_SPARSIFY_TWEIGHT || mode == GP_SPARSIFY_UNIFORM, GP_ERR_INVALID,
              "unknown sparsifier mode");
   const int n = g.n;
@@ -230,6 +231,8 @@ void sparsify_graph(gp_ctx *ctx, const DevGraph &g, int64_t m_hat, int32_t level
   }
   if (n > 0)
     GP_CUDA(cudaMemcpyAsync(out.vwgt, g.vwgt, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (trace.on())
+    fprintf(stderr, "[gp sparsify] m2=%lld -> %d ms=%.2f\n", (long long)m2, m2_out, trace.ms());
   if (st) {
     st->omega_t = wt;
     st->n_greater = ng;

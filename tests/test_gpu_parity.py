@@ -227,7 +227,7 @@ def test_rebalance_matches_oracle(gp, ctx, k):
     assert np.array_equal(t.cpu().numpy(), oblk)
 
 
-@pytest.mark.parametrize("k", [2, 4, 16, 64])
+@pytest.mark.parametrize("k", [2, 4, 16, 64, 128, 200, 300])
 def test_refine_matches_oracle(gp, ctx, k):
     import torch
     for g in (GRAPHS["er_w"], GRAPHS["rmat12"], GRAPHS["grid"]):
@@ -301,6 +301,12 @@ def test_partition_config_variants(gp, ctx, kw):
 
 def test_partition_rmat_scale15(gp, ctx):
     _check_partition(gp, ctx, gg.rmat(15, 16, seed=1), 64, 0.03, 1)
+
+
+@pytest.mark.parametrize("k", [129, 256, 300])
+def test_partition_many_blocks(gp, ctx, k):
+    # narrow (uint8) and wide block ids in refinement and the cut
+    _check_partition(gp, ctx, gg.er(60000, 300000, 7), k, 0.03, 3)
 
 
 def test_partition_host_entry_matches_device(gp, ctx):
