@@ -39,6 +39,12 @@ SMALL = dict(name="erdos_renyi_n2^20_m10485760_k128", n=1 << 20, m=10_485_760, k
 # bounded CPU sample of the same workload family (same degree, same k)
 CPU_SAMPLE = dict(name="erdos_renyi_n2^21_m20971520_k128", n=1 << 21, m=20_971_520, k=128, seed=1)
 FALLBACK_HBM_GBS = 6800.0
+# profile classes of the coarsening phase (the rest belong to initial partitioning and uncoarsening,
+# or are shared: sort, scan, round_setup)
+COARSEN_CLASSES = ("lp_rate", "lp_accept", "lp_overflow", "lp_apply", "two_hop", "relabel", "contract",
+                   "contract_aux", "sparsify")
+# ncu DRAM traffic per algorithmic byte, by class, with the sources the counters were taken on
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
 def log(*a):
@@ -67,6 +73,29 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest(files):
+    import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_ratio(cls):
+    """DRAM bytes per algorithmic byte of `cls` from a committed ncu summary, or None when that
+    summary is missing or was taken on sources that have changed since."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, "no ncu summary"
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f).get(cls)
+    if not d:
+        return None, "no ncu summary for this class"
+    if source_digest(d["sources"]) != d["digest"]:
+        return None, "kernel changed since the ncu capture"
+    return d["dram_bytes"] / d["algorithmic_bytes"], d["capture"]
 
 
 # ------------------------------------------------------------------- clocks
@@ -266,16 +295,23 @@ def run_gpu(args, world, rank, local):
         step_ms, coarsen_ms = float(t[0]), float(t[1])
     value = world * g.m * args.steps / (coarsen_ms / 1000.0)
 
-    # roofline of the dominant kernel class (by device time in the timed region)
+    # roofline of the dominant kernel class of the coarsening phase (by device time in the
+    # timed region), plus the achieved bandwidth of every class with algorithmic bytes
     peak, peak_kind = measured_peaks()
-    dom = max((k for k in prof if prof[k]["bytes"] > 0), key=lambda k: prof[k]["ms"])
+    dom = max((k for k in COARSEN_CLASSES if prof.get(k, {}).get("bytes", 0) > 0), key=lambda k: prof[k]["ms"])
     dom_ms = prof[dom]["ms"]
     achieved = prof[dom]["bytes"] / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
+    per_launch = prof[dom]["bytes"] / max(prof[dom]["launches"], 1)
+    ratio, traffic_src = traffic_ratio(dom)
+    traffic = args.traffic if args.traffic is not None else (ratio * per_launch if ratio else None)
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-            if peak_kind == "measured" else "fallback", "traffic": args.traffic,
-            "launches": prof[dom]["launches"], "ms": dom_ms,
-            "algorithmic_bytes": prof[dom]["bytes"]}
+            if peak_kind == "measured" else "fallback", "traffic": traffic, "traffic_source": traffic_src,
+            "launches": prof[dom]["launches"], "ms": dom_ms, "algorithmic_bytes": prof[dom]["bytes"],
+            "algorithmic_bytes_per_launch": per_launch,
+            "classes": {k: {"achieved_gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9, "frac": v["bytes"] / (v["ms"] / 1000.0) / 1e9 / peak,
+                            "ms": v["ms"], "launches": v["launches"]}
+                        for k, v in prof.items() if v["bytes"] > 0 and v["ms"] > 0}}
 
     # end to end through the host entry point from pinned memory
     e2e = None

@@ -284,6 +284,7 @@ void gp_profile_reset(gp_ctx *ctx) {
   for (int i = 0; i < gp::PROF_COUNT_; i++) {
     ctx->prof_ms[i] = 0;
     ctx->prof_launches[i] = 0;
+    ctx->prof_host_bytes[i] = 0;
   }
   if (ctx->d_units)
     cudaMemsetAsync(ctx->d_units, 0, sizeof(unsigned long long) * gp::PROF_COUNT_ * gp::PROF_UNITS, ctx->stream);
@@ -321,12 +322,13 @@ gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, dou
         b = 12.0 * u[0] + 4.0 * u[2] + 16.0 * u[1] + 12.0 * u[3];
         break;
       case gp::PROF_CONTRACT:
-        // per fine entry: neighbour id, weight, coarse id of the neighbour (12 B);
-        // per coarse entry written to the temporary (8 B)
-        b = 12.0 * u[0] + 8.0 * u[3];
+        // map: per fine entry neighbour id, weight, coarse id of the neighbour read (12 B) and
+        // (coarse neighbour, weight) written to the segment (8 B); merge: every segment entry
+        // read (8 B), every merged entry written (8 B)
+        b = 28.0 * u[0] + 8.0 * u[3];
         break;
       default:
-        b = 0;
+        b = ctx->prof_host_bytes[i];
     }
     if (launches) *launches = ctx->prof_launches[i];
     if (ms) *ms = ctx->prof_ms[i];

@@ -8,13 +8,19 @@ namespace gp {
 
 namespace {
 
-__global__ void k_init_clusters(const int32_t *vwgt, int n, int32_t *label, int32_t *cw, int32_t *size) {
+__global__ void k_init_clusters(const int32_t *vwgt, int n, int32_t *label, int32_t *cw) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     label[v] = (int32_t)v;
     cw[v] = vwgt[v];
-    size[v] = 1;
   }
+}
+
+// Members per cluster.
+__global__ void k_cluster_sizes(const int32_t *label, int n, int32_t *size) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&size[label[v]], 1);
 }
 
 // heaviest member of every favourite group
@@ -115,9 +121,9 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
     label_own.reset(ctx, (size_t)n);
     label = label_own.get();
   }
-  DBuf<int32_t> cw(ctx, (size_t)n), size(ctx, (size_t)n);
+  DBuf<int32_t> cw(ctx, (size_t)n);
   DBuf<int64_t> ncl_dev(ctx, 1);
-  k_init_clusters<<<grid, 256, 0, ctx->stream>>>(g.vwgt, n, label, cw.get(), size.get());
+  k_init_clusters<<<grid, 256, 0, ctx->stream>>>(g.vwgt, n, label, cw.get());
   GP_LAUNCH_CHECK();
   int64_t n64 = n;
   GP_CUDA(cudaMemcpyAsync(ncl_dev.get(), &n64, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
@@ -130,7 +136,7 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
   p.dbg_max_subrounds = cfg.dbg_max_subrounds;
   p.prof_rate = PROF_LP_RATE; p.prof_accept = PROF_LP_ACCEPT;
   p.prof_overflow = PROF_LP_OVERFLOW; p.prof_apply = PROF_LP_APPLY;
-  LpResult r = lp_run(ctx, g, label, cw.get(), size.get(), n, seed, p, ncl_dev.get());
+  LpResult r = lp_run(ctx, g, label, cw.get(), n, seed, p, ncl_dev.get());
   int64_t ncl = n == 0 ? 0 : r.nclusters;
   out.st.n = n;
   out.st.lp_subrounds = r.subrounds;
@@ -141,6 +147,10 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
   if (cfg.two_hop && 2 * ncl > n && ncl > n_min) {
     ProfScope ps(ctx, PROF_TWOHOP);
     const uint64_t kfav = stream_key(seed, TAG_FAV, (uint32_t)level, 0);
+    DBuf<int32_t> size(ctx, (size_t)n);
+    size.zero();
+    k_cluster_sizes<<<grid, 256, 0, ctx->stream>>>(label, n, size.get());
+    GP_LAUNCH_CHECK();
     DBuf<uint64_t> keys;
     int32_t count = 0;
     favourites_bucketed(ctx, g, label, size.get(), U, kfav, keys, count);

@@ -2,13 +2,19 @@
 // of its members' weights; coarse edge {A, B}, A != B, weighs the total
 // weight of the fine edges between the clusters.
 //
-// Fine nodes are bucketed by coarse id; each coarse node then aggregates the
-// (coarse neighbour, weight) pairs of all its members in a hash table (a
-// warp with a 256-slot shared-memory table when the members have at most 128
-// entries together, otherwise a block with a 4096-slot shared table or a
-// global table), writing its row into a temporary at an upper-bound offset;
-// the rows are finally packed into the coarse CSR.  Row order inside a
-// coarse row is unspecified.
+// Three passes over the fine graph, each with coalesced streams:
+//  reserve: every fine node reserves room for its row inside its coarse
+//           node's segment (an atomic add on the segment length returns the
+//           node's offset) and adds its weight to the coarse node;
+//  map    : warps walk 32 consecutive fine rows at a time (one contiguous
+//           range of entries) and write (coarse id of the neighbour, weight)
+//           into the owner's segment; entries inside the cluster are marked;
+//  merge  : each segment is summed by coarse neighbour in a hash table (a
+//           warp with a shared-memory table up to 256 entries, a block with
+//           a 4096-slot shared or a global table above) and written back in
+//           place, compacted;
+// and the merged rows are finally packed into the coarse CSR.  Row order
+// inside a coarse row is unspecified.
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -21,6 +27,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kWarpSlots = 256;
 constexpr int kWarpMaxUb = 128;
 constexpr int kBlockSmemSlots = 4096;
+constexpr int kMapUnroll = 4;
 
 __device__ __forceinline__ unsigned slot_hash(int B, int bits) {
   return ((unsigned)B * 2654435761u) >> (32 - bits);
@@ -35,38 +42,89 @@ __device__ __forceinline__ void table_add(int *tk, int *tv, int mask, int bits, 
   }
 }
 
-__global__ void k_member_count(const int32_t *xadj, const int32_t *vwgt, const int32_t *cmap, int n,
-                               int32_t *cnt, int32_t *ub, int32_t *cw) {
+__device__ __forceinline__ int table_bits(int entries) {
+  int bits = 5;
+  while ((1 << bits) < 2 * entries) bits++;
+  return bits;
+}
+
+// Segment length (the member rows' total length) and weight of every coarse
+// node; moff[v] = offset of v's row inside its coarse node's segment.
+__global__ void k_reserve(const int32_t *xadj, const int32_t *vwgt, const int32_t *cmap, int n, int32_t *seg,
+                          int32_t *cw, int32_t *moff) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int A = cmap[v];
-    atomicAdd(&cnt[A], 1);
-    atomicAdd(&ub[A], xadj[v + 1] - xadj[v]);
+    moff[v] = atomicAdd(&seg[A], xadj[v + 1] - xadj[v]);
     atomicAdd(&cw[A], vwgt[v]);
   }
 }
 
-__global__ void k_member_fill(const int32_t *cmap, int n, const int32_t *mstart, int32_t *cursor,
-                              int32_t *members) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const int A = cmap[v];
-    members[mstart[A] + atomicAdd(&cursor[A], 1)] = (int32_t)v;
+// (coarse neighbour, weight) of every fine entry into its owner's segment;
+// entries inside the owner's cluster get neighbour -1.
+__global__ void __launch_bounds__(kThreads) k_map(const int32_t *xadj, const int32_t *adjncy,
+                                                  const int32_t *adjwgt, const int32_t *cmap,
+                                                  const int32_t *moff, const int32_t *tstart, int n,
+                                                  int2 *temp, unsigned long long *units) {
+  const int lane = (int)lane_id();
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  unsigned long long ue = 0;
+  for (int64_t u0 = (int64_t)wid * 32; u0 < n; u0 += (int64_t)nw * 32) {
+    const int64_t u = u0 + lane;
+    const bool valid = u < n;
+    int xs = 0, xe = 0x7FFFFFFF, A = -2, base = 0;
+    if (valid) {
+      xs = xadj[u];
+      xe = xadj[u + 1];
+      A = cmap[u];
+      base = tstart[A] + moff[u] - xs;
+    }
+    const int e0 = __shfl_sync(FULL, xs, 0);
+    const int last = (int)((n - u0) < 32 ? (n - u0) : 32) - 1;
+    const int e1 = __shfl_sync(FULL, xe, last);
+    if (lane == 0) ue += (unsigned long long)(e1 - e0);
+    // four entries per lane in flight: ids, then coarse ids, then the writes
+    for (int f0 = e0; f0 < e1; f0 += 32 * kMapUnroll) {
+      int e[kMapUnroll], bj[kMapUnroll], Aj[kMapUnroll], nb[kMapUnroll];
+#pragma unroll
+      for (int r = 0; r < kMapUnroll; r++) {
+        e[r] = f0 + r * 32 + lane;
+        int j = 0;  // owner: lanes whose row ends at or before e
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int val = __shfl_sync(FULL, xe, j + step - 1);
+          if (val <= e[r]) j += step;
+        }
+        bj[r] = __shfl_sync(FULL, base, j);
+        Aj[r] = __shfl_sync(FULL, A, j);
+      }
+#pragma unroll
+      for (int r = 0; r < kMapUnroll; r++) nb[r] = e[r] < e1 ? adjncy[e[r]] : 0;
+#pragma unroll
+      for (int r = 0; r < kMapUnroll; r++) nb[r] = e[r] < e1 ? cmap[nb[r]] : 0;
+#pragma unroll
+      for (int r = 0; r < kMapUnroll; r++)
+        if (e[r] < e1) temp[bj[r] + e[r]] = nb[r] == Aj[r] ? make_int2(-1, 0) : make_int2(nb[r], adjwgt[e[r]]);
+    }
   }
+  ue = warp_sum(ue);
+  if (units && lane == 0) atomicAdd(units + 0, ue);
 }
 
-struct AggArgs {
-  const int32_t *xadj, *adjncy, *adjwgt, *cmap, *mstart, *members, *ub, *tstart;
+struct MergeArgs {
+  const int32_t *tstart;
   int nc;
-  int32_t *tkeys, *tvals, *rowcnt;
+  int2 *temp;
+  int32_t *rowcnt;
   int32_t *large, *nlarge;
   int32_t *gkeys, *gvals;
   int64_t gstride;
   unsigned long long *units;
 };
 
-// One warp per coarse node whose members hold <= 128 entries.
-__global__ void __launch_bounds__(kThreads) k_agg_warp(AggArgs a) {
+// One warp per coarse node whose segment holds at most kWarpMaxUb entries.
+__global__ void __launch_bounds__(kThreads) k_merge_warp(MergeArgs a) {
   __shared__ int s_k[kWarps][kWarpSlots];
   __shared__ int s_v[kWarps][kWarpSlots];
   const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
@@ -75,128 +133,79 @@ __global__ void __launch_bounds__(kThreads) k_agg_warp(AggArgs a) {
   __syncwarp();
   const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-  unsigned long long ue = 0, uout = 0;
+  unsigned long long uout = 0;
   for (int A = wid; A < a.nc; A += nw) {
-    if (a.ub[A] > kWarpMaxUb) {
+    const int s0 = a.tstart[A], s1 = a.tstart[A + 1];
+    const int len = s1 - s0;
+    if (len > kWarpMaxUb) {
       if (lane == 0) a.large[atomicAdd(a.nlarge, 1)] = A;
       continue;
     }
-    const int m0 = a.mstart[A], m1 = a.mstart[A + 1];
-    for (int mb = m0; mb < m1; mb += 32) {
-      int st = 0, d = 0;
-      if (mb + lane < m1) {
-        const int v = a.members[mb + lane];
-        st = a.xadj[v];
-        d = a.xadj[v + 1] - st;
-      }
-      int incl = d;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int excl = incl - d;
-      const int total = __shfl_sync(FULL, incl, 31);
-      ue += total;
-      for (int f0 = 0; f0 < total; f0 += 32) {
-        const int f = f0 + lane;
-        // member j of entry f: number of lanes whose inclusive end is <= f
-        int j = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int val = __shfl_sync(FULL, incl, j + step - 1);
-          if (val <= f) j += step;
-        }
-        const int sj = __shfl_sync(FULL, st, j);
-        const int ej = __shfl_sync(FULL, excl, j);
-        if (f < total) {
-          const int e = sj + (f - ej);
-          const int B = a.cmap[a.adjncy[e]];
-          if (B != A) table_add(tk, tv, kWarpSlots - 1, 8, B, a.adjwgt[e]);
-        }
-      }
+    const int bits = table_bits(len), tsize = 1 << bits;
+    for (int i0 = s0; i0 < s1; i0 += 64) {  // two entries per lane in flight
+      const int i1 = i0 + lane, i2 = i0 + 32 + lane;
+      const int2 x1 = i1 < s1 ? a.temp[i1] : make_int2(-1, 0);
+      const int2 x2 = i2 < s1 ? a.temp[i2] : make_int2(-1, 0);
+      if (x1.x >= 0) table_add(tk, tv, tsize - 1, bits, x1.x, x1.y);
+      if (x2.x >= 0) table_add(tk, tv, tsize - 1, bits, x2.x, x2.y);
     }
     __syncwarp();
-    const int base = a.tstart[A];
+    // extract in slot order and leave the table clean for the next node
     int cnt = 0;
-    for (int t0 = 0; t0 < kWarpSlots; t0 += 32) {
+    for (int t0 = 0; t0 < tsize; t0 += 32) {
       const int key = tk[t0 + lane];
       const bool occ = key >= 0;
       const unsigned m = __ballot_sync(FULL, occ);
       if (occ) {
-        const int pos = base + cnt + __popc(m & lanemask_lt());
-        a.tkeys[pos] = key;
-        a.tvals[pos] = tv[t0 + lane];
+        a.temp[s0 + cnt + __popc(m & lanemask_lt())] = make_int2(key, tv[t0 + lane]);
+        tk[t0 + lane] = -1;
+        tv[t0 + lane] = 0;
       }
       cnt += __popc(m);
-      tk[t0 + lane] = -1;
-      tv[t0 + lane] = 0;
     }
     if (lane == 0) a.rowcnt[A] = cnt;
     uout += cnt;
     __syncwarp();
   }
-  if (a.units && lane == 0) {
-    atomicAdd(a.units + 0, ue);
-    atomicAdd(a.units + 3, uout);
-  }
+  if (a.units && lane == 0) atomicAdd(a.units + 3, uout);
 }
 
 // One block per coarse node of the large list.
-__global__ void __launch_bounds__(kThreads) k_agg_block(AggArgs a) {
+__global__ void __launch_bounds__(kThreads) k_merge_block(MergeArgs a) {
   __shared__ int s_k[kBlockSmemSlots];
   __shared__ int s_v[kBlockSmemSlots];
   __shared__ int s_cnt;
-  for (int t = threadIdx.x; t < kBlockSmemSlots; t += blockDim.x) { s_k[t] = -1; s_v[t] = 0; }
-  __syncthreads();
   const int nl = *a.nlarge;
   int *gk = a.gkeys ? a.gkeys + (int64_t)blockIdx.x * a.gstride : nullptr;
   int *gv = a.gvals ? a.gvals + (int64_t)blockIdx.x * a.gstride : nullptr;
-  const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
-  unsigned long long ue = 0, uout = 0;
+  unsigned long long uout = 0;
   for (int li = blockIdx.x; li < nl; li += gridDim.x) {
     const int A = a.large[li];
-    const int ub = a.ub[A];
-    int bits = 1;
-    while ((1 << bits) < 2 * ub) bits++;
-    const int tsize = 1 << bits;
+    const int s0 = a.tstart[A], s1 = a.tstart[A + 1];
+    const int bits = table_bits(s1 - s0), tsize = 1 << bits;
     const bool in_smem = tsize <= kBlockSmemSlots;
     int *tk = in_smem ? s_k : gk;
     int *tv = in_smem ? s_v : gv;
-    const int m0 = a.mstart[A], m1 = a.mstart[A + 1];
-    for (int mi = m0 + wib; mi < m1; mi += kWarps) {
-      const int v = a.members[mi];
-      const int st = a.xadj[v], en = a.xadj[v + 1];
-      for (int e = st + lane; e < en; e += 32) {
-        const int B = a.cmap[a.adjncy[e]];
-        if (B != A) table_add(tk, tv, tsize - 1, bits, B, a.adjwgt[e]);
-      }
-    }
+    for (int t = threadIdx.x; t < tsize; t += blockDim.x) { tk[t] = -1; tv[t] = 0; }
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    const int base = a.tstart[A];
+    for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+      const int2 x = a.temp[i];
+      if (x.x >= 0) table_add(tk, tv, tsize - 1, bits, x.x, x.y);
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
       const int key = tk[t];
-      if (key >= 0) {
-        const int pos = atomicAdd(&s_cnt, 1);
-        a.tkeys[base + pos] = key;
-        a.tvals[base + pos] = tv[t];
-        tk[t] = -1;
-        tv[t] = 0;
-      }
+      if (key >= 0) a.temp[s0 + atomicAdd(&s_cnt, 1)] = make_int2(key, tv[t]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       a.rowcnt[A] = s_cnt;
-      ue += ub;
       uout += s_cnt;
     }
     __syncthreads();
   }
-  if (a.units && threadIdx.x == 0) {
-    atomicAdd(a.units + 0, ue);
-    atomicAdd(a.units + 3, uout);
-  }
+  if (a.units && threadIdx.x == 0) atomicAdd(a.units + 3, uout);
 }
 
 __global__ void k_max_i32(const int32_t *x, int n, int *out) {
@@ -208,10 +217,9 @@ __global__ void k_max_i32(const int32_t *x, int n, int *out) {
   if (lane_id() == 0 && m) atomicMax(out, m);
 }
 
-// Packs the rows from the upper-bound layout into the final CSR.
+// Packs the merged rows from the segment layout into the final CSR.
 __global__ void __launch_bounds__(kThreads) k_pack_rows(const int32_t *tstart, const int32_t *rowcnt,
-                                                        const int32_t *xadj_out, int nc,
-                                                        const int32_t *tkeys, const int32_t *tvals,
+                                                        const int32_t *xadj_out, int nc, const int2 *temp,
                                                         int32_t *adj, int32_t *w) {
   const int lane = (int)lane_id();
   const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -219,8 +227,9 @@ __global__ void __launch_bounds__(kThreads) k_pack_rows(const int32_t *tstart, c
   for (int A = wid; A < nc; A += nw) {
     const int src = tstart[A], dst = xadj_out[A], c = rowcnt[A];
     for (int j = lane; j < c; j += 32) {
-      adj[dst + j] = tkeys[src + j];
-      w[dst + j] = tvals[src + j];
+      const int2 x = temp[src + j];
+      adj[dst + j] = x.x;
+      w[dst + j] = x.y;
     }
   }
 }
@@ -231,53 +240,51 @@ void contract_graph(gp_ctx *ctx, const DevGraph &g, const int32_t *cmap, int32_t
   TraceTimer trace(ctx);
   const int n = g.n;
   const int grid = grid_for(n, 256, ctx->num_sms * 8);
-  DBuf<int32_t> cnt(ctx, (size_t)nc + 1), ub(ctx, (size_t)nc + 1), cw(ctx, (size_t)nc + 1);
-  DBuf<int32_t> mstart(ctx, (size_t)nc + 1), tstart(ctx, (size_t)nc + 1), cursor(ctx, (size_t)nc + 1);
-  DBuf<int32_t> members(ctx, (size_t)n);
+  DBuf<int32_t> seg(ctx, (size_t)nc + 1), cw(ctx, (size_t)nc + 1), tstart(ctx, (size_t)nc + 1);
+  DBuf<int32_t> moff(ctx, (size_t)(n > 0 ? n : 1));
   {
     ProfScope ps(ctx, PROF_CONTRACT_AUX);
-    cnt.zero(); ub.zero(); cw.zero(); cursor.zero();
-    k_member_count<<<grid, 256, 0, ctx->stream>>>(g.xadj, g.vwgt, cmap, n, cnt.get(), ub.get(), cw.get());
+    seg.zero(); cw.zero();
+    k_reserve<<<grid, 256, 0, ctx->stream>>>(g.xadj, g.vwgt, cmap, n, seg.get(), cw.get(), moff.get());
     GP_LAUNCH_CHECK();
-    scan_exclusive_i32(ctx, cnt.get(), mstart.get(), nc + 1, nullptr);
-    scan_exclusive_i32(ctx, ub.get(), tstart.get(), nc + 1, nullptr);
-    k_member_fill<<<grid, 256, 0, ctx->stream>>>(cmap, n, mstart.get(), cursor.get(), members.get());
-    GP_LAUNCH_CHECK();
+    scan_exclusive_i32(ctx, seg.get(), tstart.get(), nc + 1, nullptr);
   }
-  DBuf<int32_t> tkeys(ctx, (size_t)(g.m2 > 0 ? g.m2 : 1)), tvals(ctx, (size_t)(g.m2 > 0 ? g.m2 : 1));
+  DBuf<int2> temp(ctx, (size_t)(g.m2 > 0 ? g.m2 : 1));
   DBuf<int32_t> rowcnt(ctx, (size_t)nc + 1), large(ctx, (size_t)nc + 1), nlarge(ctx, 1);
   rowcnt.zero();
   nlarge.zero();
-  AggArgs a{};
-  a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.cmap = cmap;
-  a.mstart = mstart.get(); a.members = members.get(); a.ub = ub.get(); a.tstart = tstart.get();
-  a.nc = nc; a.tkeys = tkeys.get(); a.tvals = tvals.get(); a.rowcnt = rowcnt.get();
+  MergeArgs a{};
+  a.tstart = tstart.get(); a.nc = nc; a.temp = temp.get(); a.rowcnt = rowcnt.get();
   a.large = large.get(); a.nlarge = nlarge.get();
-  a.units = ctx->d_units ? ctx->d_units + PROF_CONTRACT * PROF_UNITS : nullptr;
+  unsigned long long *units = ctx->d_units ? ctx->d_units + PROF_CONTRACT * PROF_UNITS : nullptr;
+  a.units = units;
   // global tables when some coarse node needs more than the shared table
-  DBuf<int> maxub(ctx, 1);
-  maxub.zero();
-  k_max_i32<<<grid_for(nc, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(ub.get(), nc, maxub.get());
+  DBuf<int> maxseg(ctx, 1);
+  maxseg.zero();
+  k_max_i32<<<grid_for(nc, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(seg.get(), nc, maxseg.get());
   GP_LAUNCH_CHECK();
-  const int mub = read_scalar(ctx, maxub.get());
+  const int mseg = read_scalar(ctx, maxseg.get());
   int bits = 1;
-  while ((1 << bits) < 2 * mub) bits++;
+  while ((1 << bits) < 2 * mseg) bits++;
   const int lblocks = ctx->num_sms * 4;
   DBuf<int32_t> gk, gv;
   if ((1 << bits) > kBlockSmemSlots) {
     a.gstride = (int64_t)1 << bits;
     gk.reset(ctx, (size_t)(a.gstride * lblocks));
     gv.reset(ctx, (size_t)(a.gstride * lblocks));
-    gk.fill_bytes(0xFF);
-    gv.zero();
     a.gkeys = gk.get();
     a.gvals = gv.get();
   }
   {
     ProfScope ps(ctx, PROF_CONTRACT);
-    k_agg_warp<<<grid_for((int64_t)nc * 32, kThreads, ctx->num_sms * 8), kThreads, 0, ctx->stream>>>(a);
+    if (n > 0) {
+      k_map<<<grid_for((int64_t)n, kThreads, ctx->num_sms * 16), kThreads, 0, ctx->stream>>>(
+          g.xadj, g.adjncy, g.adjwgt, cmap, moff.get(), tstart.get(), n, temp.get(), units);
+      GP_LAUNCH_CHECK();
+    }
+    k_merge_warp<<<grid_for((int64_t)nc * 32, kThreads, ctx->num_sms * 8), kThreads, 0, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
-    k_agg_block<<<lblocks, kThreads, 0, ctx->stream>>>(a);
+    k_merge_block<<<lblocks, kThreads, 0, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
   }
   DBuf<int32_t> total(ctx, 1);
@@ -294,7 +301,7 @@ void contract_graph(gp_ctx *ctx, const DevGraph &g, const int32_t *cmap, int32_t
   {
     ProfScope ps(ctx, PROF_CONTRACT_AUX);
     k_pack_rows<<<grid_for((int64_t)nc * 32, kThreads, ctx->num_sms * 8), kThreads, 0, ctx->stream>>>(
-        tstart.get(), rowcnt.get(), out.xadj, nc, tkeys.get(), tvals.get(), out.adjncy, out.adjwgt);
+        tstart.get(), rowcnt.get(), out.xadj, nc, temp.get(), out.adjncy, out.adjwgt);
     GP_LAUNCH_CHECK();
   }
   out.bv.reset(ctx, (size_t)nc);

@@ -104,6 +104,7 @@ struct gp_ctx {
   double prof_ms[gp::PROF_COUNT_] = {};
   int64_t prof_launches[gp::PROF_COUNT_] = {};
   unsigned long long *d_units = nullptr;  // PROF_COUNT_ x PROF_UNITS
+  double prof_host_bytes[gp::PROF_COUNT_] = {};  // algorithmic bytes of classes sized on the host
 };
 
 namespace gp {
@@ -162,6 +163,11 @@ T read_scalar(gp_ctx *ctx, const T *dev) {
 }
 
 // ------------------------------------------------------------- profiling
+
+// Adds algorithmic bytes to a class whose sizes the host knows (profiling only).
+inline void prof_bytes(gp_ctx *ctx, int cls, double bytes) {
+  if (ctx->profile) ctx->prof_host_bytes[cls] += bytes;
+}
 
 struct ProfScope {
   gp_ctx *ctx;

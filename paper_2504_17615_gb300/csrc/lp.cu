@@ -12,9 +12,9 @@
 //            the bound accepts everybody; the proposers of overflowing
 //            targets are sorted by (target, h32(PRIO), node) and accepted
 //            while the running weight fits (longest prefix)
-//   apply  : labels, weights and cluster sizes are updated; emptied
-//            clusters are counted; the stop flag is raised when the cluster
-//            count reaches n_min or a round moved nothing.
+//   apply  : labels and weights are updated; the non-empty clusters (the
+//            labels of positive weight) are counted; the stop flag is raised
+//            when that count reaches n_min or a round moved nothing.
 #include "lp.cuh"
 
 namespace gp {
@@ -193,33 +193,57 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
       for (int q = 0; q < U; q++)
         own_r[q] = __reduce_max_sync(gmask, (lead[q] && L[q] == own[q]) ? sum[q] : 0);
     }
+    // choose: all U sets advance together, so that the weight reads of their
+    // leading candidates are issued side by side
+    bool alive[U], searching[U];
+    unsigned best[U];
 #pragma unroll
     for (int q = 0; q < U; q++) {
-      bool alive = lead[q] && L[q] != own[q];
-      uc += alive;
-      unsigned best = 0xFFFFFFFFu;
-      bool searching = v[q] >= 0;
-      while (__any_sync(FULL, searching)) {
-        const int r = __reduce_max_sync(gmask, (searching && alive) ? sum[q] : -1);
-        if (r < 0 || (MODE == RATE_LP && r <= own_r[q])) searching = false;
-        const bool top = searching && alive && sum[q] == r;
+      alive[q] = lead[q] && L[q] != own[q];
+      uc += alive[q];
+      searching[q] = v[q] >= 0;
+      best[q] = 0xFFFFFFFFu;
+    }
+    for (int it = 0; it <= G; it++) {  // bounded: every pass drops one candidate per searching group
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < U; q++) any = any || searching[q];
+      if (!__any_sync(FULL, any)) break;
+      unsigned c[U];
+      bool holder[U];
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int r = __reduce_max_sync(gmask, (searching[q] && alive[q]) ? sum[q] : -1);
+        if (r < 0 || (MODE == RATE_LP && r <= own_r[q])) searching[q] = false;
+        const bool top = searching[q] && alive[q] && sum[q] == r;
         const unsigned h = top ? h32(a.ktie, (uint32_t)v[q], (uint32_t)L[q]) : 0xFFFFFFFFu;
         const unsigned hmin = __reduce_min_sync(gmask, h);
-        const unsigned c = __reduce_min_sync(gmask, (top && h == hmin) ? (unsigned)L[q] : 0xFFFFFFFFu);
-        if (MODE != RATE_LP) {
-          if (searching) { best = c; searching = false; }
-        } else {
-          const bool holder = top && h == hmin && (unsigned)L[q] == c;
-          const unsigned fits = holder && (int64_t)a.weight[c] + cv[q] <= a.bound ? 1u : 0u;
-          if (searching && __reduce_or_sync(gmask, fits)) { best = c; searching = false; }
-          alive = alive && (unsigned)L[q] != c;
+        c[q] = __reduce_min_sync(gmask, (top && h == hmin) ? (unsigned)L[q] : 0xFFFFFFFFu);
+        holder[q] = top && h == hmin && (unsigned)L[q] == c[q];
+      }
+      if (MODE != RATE_LP) {
+#pragma unroll
+        for (int q = 0; q < U; q++)
+          if (searching[q]) { best[q] = c[q]; searching[q] = false; }
+      } else {
+        int wc[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) wc[q] = holder[q] ? a.weight[c[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          const unsigned fits = holder[q] && (int64_t)wc[q] + cv[q] <= a.bound ? 1u : 0u;
+          if (__reduce_or_sync(gmask, fits) && searching[q]) { best[q] = c[q]; searching[q] = false; }
+          alive[q] = alive[q] && (unsigned)L[q] != c[q];
         }
       }
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) {
       if (gl == 0 && v[q] >= 0) {
         ue += deg[q];
         uv += 1;
-        if (best != 0xFFFFFFFFu) {
-          emit<MODE>(a, base + q * NV + grp, v[q], (int)best, cv[q]);
+        if (best[q] != 0xFFFFFFFFu) {
+          emit<MODE>(a, base + q * NV + grp, v[q], (int)best[q], cv[q]);
           up += 1;
         }
       }
@@ -479,7 +503,7 @@ struct Counters {
   long long moved_sub;
   long long moved_round;
   long long moved_total;
-  long long emptied;
+  long long nonempty;   // labels of positive weight, counted after the sub-round's moves
   long long nclusters;
 };
 
@@ -579,6 +603,130 @@ __global__ void k_ov_accept(const uint64_t *keys, const uint32_t *vals, int n, c
   }
 }
 
+// ------------------------------------------ overflow with few labels
+//
+// The proposers of overflowing targets are not sorted.  Per target, a
+// histogram of their weights over the top bits of the priority locates the
+// bucket in which the running weight (in priority order) crosses the
+// target's free room: proposers in earlier buckets fit (the accepted prefix
+// contains them), proposers in later ones do not, and only the crossing
+// bucket's proposers are ranked exactly by (priority, node), in one block per
+// target.  The result equals the longest-prefix rule of the sorted order.
+
+constexpr int kOvBuckets = 4096;   // priority buckets per label (top 12 bits)
+constexpr int kOvMaxLabels = 256;  // labels handled this way
+constexpr int kOvSmem = 2048;      // crossing-bucket proposers ranked in shared memory
+
+__global__ void k_ovb_hist(const uint64_t *key, const uint32_t *val, int nov, const int32_t *vwgt,
+                           unsigned long long *hw, int32_t *hc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nov; i += gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    const int64_t slot = (int64_t)(k >> 32) * kOvBuckets + (int)((uint32_t)k >> 20);
+    atomicAdd(&hw[slot], (unsigned long long)vwgt[val[i]]);
+    atomicAdd(&hc[slot], 1);
+  }
+}
+
+// One block per label: the crossing bucket, the weight before it and the
+// number of proposers in it.
+__global__ void __launch_bounds__(256) k_ovb_cut(const unsigned long long *hw, const int32_t *hc,
+                                                 const int32_t *weight, int64_t bound, int32_t *cut,
+                                                 long long *base, int32_t *mcnt) {
+  constexpr int PER = kOvBuckets / 256;
+  __shared__ long long s_w[8];
+  __shared__ int s_cut;
+  const int K = blockIdx.x;
+  const unsigned long long *h = hw + (int64_t)K * kOvBuckets;
+  const int t = threadIdx.x, lane = (int)lane_id(), wp = t >> 5;
+  long long loc = 0;
+#pragma unroll
+  for (int q = 0; q < PER; q++) loc += (long long)h[t * PER + q];
+  long long incl = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_w[wp] = incl;
+  if (t == 0) s_cut = kOvBuckets;
+  __syncthreads();
+  long long excl = incl - loc;
+  for (int q = 0; q < wp; q++) excl += s_w[q];
+  const long long room = bound - (long long)weight[K];
+  long long run = excl;
+  int mine = kOvBuckets;
+  long long before = 0;
+  for (int q = 0; q < PER; q++) {
+    const long long x = (long long)h[t * PER + q];
+    if (x > 0 && run + x > room) { mine = t * PER + q; before = run; break; }
+    run += x;
+  }
+  if (mine < kOvBuckets) atomicMin(&s_cut, mine);
+  __syncthreads();
+  if (mine == s_cut && mine < kOvBuckets) {
+    cut[K] = mine;
+    base[K] = before;
+    mcnt[K] = hc[(int64_t)K * kOvBuckets + mine];
+  }
+  if (t == 0 && s_cut == kOvBuckets) { cut[K] = kOvBuckets; base[K] = 0; mcnt[K] = 0; }
+}
+
+__global__ void __launch_bounds__(1024) k_ovb_offsets(const int32_t *mcnt, int nlabels, int32_t *roff,
+                                                      int32_t *cursor) {
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int K = 0; K < nlabels; K++) { roff[K] = run; cursor[K] = run; run += mcnt[K]; }
+    roff[nlabels] = run;
+  }
+}
+
+// Earlier buckets accepted, later ones rejected, the crossing bucket's
+// proposers listed per label.
+__global__ void k_ovb_class(const uint64_t *key, const uint32_t *val, int nov, const int32_t *cut,
+                            int32_t *cursor, uint8_t *acc, uint64_t *bkey, int32_t *bidx) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nov; i += gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    const int K = (int)(k >> 32), b = (int)((uint32_t)k >> 20), c = cut[K];
+    acc[i] = b < c ? 1 : 0;
+    if (b == c) {
+      const int j = atomicAdd(&cursor[K], 1);
+      bkey[j] = ((uint64_t)(uint32_t)k << 32) | val[i];  // (priority, node)
+      bidx[j] = i;
+    }
+  }
+}
+
+// One block per label: ranks the crossing bucket's proposers by (priority,
+// node) and accepts those whose running weight still fits.
+__global__ void __launch_bounds__(256) k_ovb_resolve(const uint64_t *bkey, const int32_t *bidx,
+                                                     const int32_t *roff, const int32_t *vwgt,
+                                                     const int32_t *weight, const long long *base,
+                                                     int64_t bound, uint8_t *acc) {
+  __shared__ uint64_t s_k[kOvSmem];
+  __shared__ int s_c[kOvSmem];
+  const int K = blockIdx.x;
+  const int r0 = roff[K], m = roff[K + 1] - r0;
+  if (m == 0) return;
+  const bool in_smem = m <= kOvSmem;
+  if (in_smem) {
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      s_k[j] = bkey[r0 + j];
+      s_c[j] = vwgt[(uint32_t)bkey[r0 + j]];
+    }
+    __syncthreads();
+  }
+  const long long room = bound - (long long)weight[K] - base[K];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const uint64_t ki = in_smem ? s_k[i] : bkey[r0 + i];
+    long long incl = 0;
+    for (int j = 0; j < m; j++) {  // weight of the proposers up to and including i
+      const uint64_t kj = in_smem ? s_k[j] : bkey[r0 + j];
+      if (kj <= ki) incl += in_smem ? s_c[j] : vwgt[(uint32_t)kj];
+    }
+    acc[bidx[r0 + i]] = incl <= room ? 1 : 0;
+  }
+}
+
 struct ApplyArgs {
   const int32_t *mov_v, *mov_k;
   const uint64_t *ov_key;
@@ -586,10 +734,8 @@ struct ApplyArgs {
   const uint8_t *ov_acc;
   int nmov, nov;
   const int32_t *vwgt;
-  int32_t *label, *weight, *size, *leave_cnt, *incoming;
+  int32_t *label, *weight, *incoming;
   uint8_t *label8;
-  int32_t *own;      // per proposer: the label it left (first leavers only)
-  uint8_t *first;    // per proposer: first to leave its label this sub-round
   int nshared;       // > 0: few labels; weight changes summed per block in shared memory
   Counters *cnt;
 };
@@ -614,16 +760,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
     int v, K;
     bool mv;
     proposal(a, t, v, K, mv);
-    uint8_t first = 0;
     if (mv) {
       const int own = a.label[v], c = a.vwgt[v];
       a.label[v] = K;
       if (a.label8) a.label8[v] = (uint8_t)K;
-      if (a.size) {
-        atomicAdd(&a.size[K], 1);
-        atomicSub(&a.size[own], 1);
-        if (atomicAdd(&a.leave_cnt[own], 1) == 0) { first = 1; a.own[t] = own; }
-      }
       if (a.nshared) {
         atomicAdd(&s_dw[K], c);
         atomicSub(&s_dw[own], c);
@@ -633,7 +773,6 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
       }
       moved++;
     }
-    if (a.size) a.first[t] = first;
   }
   if (a.nshared) {
     __syncthreads();
@@ -645,30 +784,37 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
     atomicAdd((unsigned long long *)&a.cnt->moved_sub, (unsigned long long)moved);
 }
 
-// Clears the incoming weights, counts the clusters the moves emptied.
+// Clears the incoming weights of the sub-round's targets.
 __global__ void __launch_bounds__(kThreads) k_finalize(ApplyArgs a) {
   const int total = a.nmov + a.nov;
-  long long emptied = 0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    int v, K;
-    bool mv;
-    proposal(a, t, v, K, mv);
+    const int K = t < a.nmov ? a.mov_k[t] : (int)(a.ov_key[t - a.nmov] >> 32);
     a.incoming[K] = 0;
-    if (a.size && a.first[t]) {
-      const int own = a.own[t];
-      if (a.size[own] == 0) emptied++;
-      a.leave_cnt[own] = 0;
-    }
   }
-  emptied = warp_sum(emptied);
-  if (lane_id() == 0 && emptied)
-    atomicAdd((unsigned long long *)&a.cnt->emptied, (unsigned long long)emptied);
+}
+
+// Non-empty clusters: node weights are positive, so a label is in use iff its weight is.
+__global__ void __launch_bounds__(kThreads) k_count_nonempty(const int32_t *weight, int64_t nlabels,
+                                                             Counters *cnt) {
+  if (cnt->stop) return;
+  long long c = 0;
+  const int4 *w4 = reinterpret_cast<const int4 *>(weight);
+  const int64_t n4 = nlabels / 4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 x = w4[i];
+    c += (x.x > 0) + (x.y > 0) + (x.z > 0) + (x.w > 0);
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlabels;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += weight[i] > 0;
+  c = warp_sum(c);
+  if (lane_id() == 0 && c) atomicAdd((unsigned long long *)&cnt->nonempty, (unsigned long long)c);
 }
 
 __global__ void k_subround_end(Counters *cnt, int count_clusters, long long n_min) {
   if (cnt->stop) return;
-  cnt->nclusters -= cnt->emptied;
-  cnt->emptied = 0;
+  if (count_clusters) cnt->nclusters = cnt->nonempty;
+  cnt->nonempty = 0;
   cnt->moved_round += cnt->moved_sub;
   cnt->moved_total += cnt->moved_sub;
   cnt->moved_sub = 0;
@@ -683,7 +829,7 @@ __global__ void k_round_end(Counters *cnt) {
 
 __global__ void k_counters_init(Counters *cnt, long long nclusters) {
   cnt->stop = 0; cnt->nov = 0; cnt->nmov = 0; cnt->pad0 = 0; cnt->moved_sub = 0; cnt->moved_round = 0;
-  cnt->moved_total = 0; cnt->emptied = 0; cnt->nclusters = nclusters;
+  cnt->moved_total = 0; cnt->nonempty = 0; cnt->nclusters = nclusters;
 }
 
 __global__ void k_reset_lists(Counters *cnt) { cnt->nov = 0; cnt->nmov = 0; }
@@ -774,8 +920,7 @@ int bits_for(int64_t x) {
   return b < 1 ? 1 : b;
 }
 
-LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int32_t *size,
-                int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev,
+LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev,
                 uint8_t *label8) {
   LpResult res;
   const int n = g.n;
@@ -788,13 +933,22 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   DBuf<uint64_t> ov_key(ctx, (size_t)n);
   DBuf<uint32_t> ov_val(ctx, (size_t)n);
   DBuf<uint8_t> ov_acc(ctx, (size_t)n);
-  DBuf<int32_t> leave_cnt, own_of;
-  DBuf<uint8_t> first;
-  if (size) {
-    leave_cnt.reset(ctx, (size_t)nlabels);
-    leave_cnt.zero();
-    own_of.reset(ctx, (size_t)n);
-    first.reset(ctx, (size_t)n);
+  // few labels (refinement): bucketed overflow resolution, no sort
+  const bool few = nlabels <= kOvMaxLabels;
+  DBuf<unsigned long long> ovb_hw;
+  DBuf<int32_t> ovb_hc, ovb_cut, ovb_m, ovb_roff, ovb_cursor, ovb_idx;
+  DBuf<long long> ovb_base;
+  DBuf<uint64_t> ovb_key;
+  if (few) {
+    ovb_hw.reset(ctx, (size_t)nlabels * kOvBuckets);
+    ovb_hc.reset(ctx, (size_t)nlabels * kOvBuckets);
+    ovb_cut.reset(ctx, (size_t)nlabels);
+    ovb_m.reset(ctx, (size_t)nlabels);
+    ovb_roff.reset(ctx, (size_t)nlabels + 1);
+    ovb_cursor.reset(ctx, (size_t)nlabels);
+    ovb_base.reset(ctx, (size_t)nlabels);
+    ovb_key.reset(ctx, (size_t)n);
+    ovb_idx.reset(ctx, (size_t)n);
   }
   DBuf<Counters> counters(ctx, 1);
   Counters *C = counters.get();
@@ -820,7 +974,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
     const uint64_t kprio = stream_key(seed, p.tag_prio, (uint32_t)p.level, (uint32_t)r);
     {
       ProfScope ps(ctx, PROF_ROUND_SETUP);
-      BucketArgs b{g.xadj, label, size, g.vwgt, n, kact, S, 0, 0, &C->stop};
+      BucketArgs b{g.xadj, label, nullptr, g.vwgt, n, kact, S, 0, 0, &C->stop};
       cnt.zero();
       k_bucket_count<<<grid_for(n, kThreads, grid), kThreads, 0, ctx->stream>>>(b, nkeys, cnt.get());
       GP_LAUNCH_CHECK();
@@ -859,7 +1013,28 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       res.overflow_total += nov;
       if (nov > res.overflow_max) res.overflow_max = nov;
       res.proposals += nov + nmov;
-      if (nov > 0) {
+      if (nov > 0 && few) {
+        ProfScope ps(ctx, p.prof_overflow);
+        const int gsmall = grid_for(nov, 256, grid);
+        GP_CUDA(cudaMemsetAsync(ovb_hw.get(), 0, sizeof(unsigned long long) * ovb_hw.count, ctx->stream));
+        GP_CUDA(cudaMemsetAsync(ovb_hc.get(), 0, sizeof(int32_t) * ovb_hc.count, ctx->stream));
+        k_ovb_hist<<<gsmall, 256, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov, g.vwgt, ovb_hw.get(),
+                                                    ovb_hc.get());
+        GP_LAUNCH_CHECK();
+        k_ovb_cut<<<(int)nlabels, 256, 0, ctx->stream>>>(ovb_hw.get(), ovb_hc.get(), weight, p.bound,
+                                                        ovb_cut.get(), ovb_base.get(), ovb_m.get());
+        GP_LAUNCH_CHECK();
+        k_ovb_offsets<<<1, 32, 0, ctx->stream>>>(ovb_m.get(), (int)nlabels, ovb_roff.get(), ovb_cursor.get());
+        GP_LAUNCH_CHECK();
+        k_ovb_class<<<gsmall, 256, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov, ovb_cut.get(),
+                                                     ovb_cursor.get(), ov_acc.get(), ovb_key.get(),
+                                                     ovb_idx.get());
+        GP_LAUNCH_CHECK();
+        k_ovb_resolve<<<(int)nlabels, 256, 0, ctx->stream>>>(ovb_key.get(), ovb_idx.get(), ovb_roff.get(),
+                                                            g.vwgt, weight, ovb_base.get(), p.bound,
+                                                            ov_acc.get());
+        GP_LAUNCH_CHECK();
+      } else if (nov > 0) {
         ProfScope ps(ctx, p.prof_overflow);
         const int kbits = bits_for(nlabels) + 32;
         radix_sort_pairs(ctx, ov_key.get(), ov_val.get(), nov, kbits);
@@ -879,14 +1054,18 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         ApplyArgs aa{};
         aa.mov_v = mov_v.get(); aa.mov_k = mov_k.get(); aa.ov_key = ov_key.get(); aa.ov_val = ov_val.get();
         aa.ov_acc = ov_acc.get(); aa.nmov = nmov; aa.nov = nov; aa.vwgt = g.vwgt; aa.label = label;
-        aa.weight = weight; aa.size = size; aa.leave_cnt = leave_cnt.get(); aa.incoming = incoming.get();
-        aa.label8 = label8; aa.own = own_of.get(); aa.first = first.get();
+        aa.weight = weight; aa.incoming = incoming.get(); aa.label8 = label8;
         aa.nshared = agg ? (int)nlabels : 0; aa.cnt = C;
         const int ga = grid_for((int64_t)nmov + nov, kThreads, grid);
         if (nmov + nov > 0) {
           k_apply<<<ga, kThreads, sizeof(int) * aa.nshared, ctx->stream>>>(aa);
           GP_LAUNCH_CHECK();
           k_finalize<<<ga, kThreads, 0, ctx->stream>>>(aa);
+          GP_LAUNCH_CHECK();
+        }
+        if (p.count_clusters) {
+          k_count_nonempty<<<grid_for(nlabels / 4 + 1, kThreads, grid), kThreads, 0, ctx->stream>>>(weight, nlabels,
+                                                                                                  C);
           GP_LAUNCH_CHECK();
         }
         k_subround_end<<<1, 1, 0, ctx->stream>>>(C, p.count_clusters ? 1 : 0, (long long)p.n_min);

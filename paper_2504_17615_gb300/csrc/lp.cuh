@@ -43,7 +43,7 @@ struct LpResult {
 // (clustering only).
 // label8 (may be null): a uint8 copy of label, used for the gathers and kept
 // in step (fewer than 256 labels).
-LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int32_t *size,
+LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
                 int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev,
                 uint8_t *label8 = nullptr);
 

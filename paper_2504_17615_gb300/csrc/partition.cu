@@ -49,34 +49,58 @@ __device__ __forceinline__ unsigned long long pair_hash(uint32_t lo, uint32_t hi
 // increasing rows, and symmetry by comparing, over the entries below and
 // above the diagonal, their counts and the sums of a 64-bit hash of
 // (min, max, weight) (equal sums unless the graph is asymmetric, up to a
-// 2^-64 collision).
+// 2^-64 collision).  Runs after the row offsets were checked; a warp walks 32
+// consecutive rows (one contiguous range of entries) at a time.
+constexpr int kValUnroll = 4;
+
 __global__ void __launch_bounds__(256) k_validate_entries(const int32_t *xadj, const int32_t *adjncy,
                                                           const int32_t *adjwgt, int n, int64_t m2,
                                                           ValOut *o) {
   const int lane = (int)lane_id();
-  const int64_t chunk = 1024;
-  const int64_t nchunks = (m2 + chunk - 1) / chunk;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   int err = 0;
   unsigned long long ws = 0, hlo = 0, hhi = 0, nlo = 0, nhi = 0;
-  for (int64_t c = wid; c < nchunks; c += nw) {
-    const int64_t e0 = c * chunk;
-    const int64_t e1 = e0 + chunk < m2 ? e0 + chunk : m2;
-    int row = 0;
-    if (lane == 0) row = row_of(xadj, n, e0);
-    row = __shfl_sync(FULL, row, 0);
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-      while (row < n - 1 && (int64_t)xadj[row + 1] <= e) row++;
-      const int v = adjncy[e];
-      const int w = adjwgt[e];
-      if (v < 0 || v >= n) { err |= VE_RANGE; continue; }
-      if (v == row) err |= VE_LOOP;
-      if (w <= 0) err |= VE_AWGT;
-      ws += (unsigned long long)(w > 0 ? w : 0);
-      if (e > xadj[row] && adjncy[e - 1] >= v) err |= VE_ORDER;
-      if (row < v) { hlo += pair_hash((uint32_t)row, (uint32_t)v, w); nlo++; }
-      else { hhi += pair_hash((uint32_t)v, (uint32_t)row, w); nhi++; }
+  for (int64_t u0 = (int64_t)wid * 32; u0 < n; u0 += (int64_t)nw * 32) {
+    const int64_t u = u0 + lane;
+    const bool valid = u < n;
+    const int xs = valid ? xadj[u] : 0x7FFFFFFF;
+    const int xe = valid ? xadj[u + 1] : 0x7FFFFFFF;
+    const int e0 = __shfl_sync(FULL, xs, 0);
+    const int last = (int)((n - u0) < 32 ? (n - u0) : 32) - 1;
+    const int e1 = __shfl_sync(FULL, xe, last);
+    for (int f0 = e0; f0 < e1; f0 += 32 * kValUnroll) {
+      int e[kValUnroll], row[kValUnroll], rs[kValUnroll], v[kValUnroll], w[kValUnroll], pv[kValUnroll];
+#pragma unroll
+      for (int r = 0; r < kValUnroll; r++) {
+        e[r] = f0 + r * 32 + lane;
+        int q = 0;  // owner: lanes whose row ends at or before e
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int val = __shfl_sync(FULL, xe, q + step - 1);
+          if (val <= e[r]) q += step;
+        }
+        row[r] = (int)(u0 + q);
+        rs[r] = __shfl_sync(FULL, xs, q);
+      }
+#pragma unroll
+      for (int r = 0; r < kValUnroll; r++) {
+        const bool in = e[r] < e1;
+        v[r] = in ? adjncy[e[r]] : 0;
+        w[r] = in ? adjwgt[e[r]] : 1;
+        pv[r] = in && e[r] > rs[r] ? adjncy[e[r] - 1] : -1;
+      }
+#pragma unroll
+      for (int r = 0; r < kValUnroll; r++) {
+        if (e[r] >= e1) continue;
+        if (v[r] < 0 || v[r] >= n) { err |= VE_RANGE; continue; }
+        if (v[r] == row[r]) err |= VE_LOOP;
+        if (w[r] <= 0) err |= VE_AWGT;
+        ws += (unsigned long long)(w[r] > 0 ? w[r] : 0);
+        if (pv[r] >= v[r]) err |= VE_ORDER;
+        if (row[r] < v[r]) { hlo += pair_hash((uint32_t)row[r], (uint32_t)v[r], w[r]); nlo++; }
+        else { hhi += pair_hash((uint32_t)v[r], (uint32_t)row[r], w[r]); nhi++; }
+      }
     }
   }
   ws = warp_sum(ws); hlo = warp_sum(hlo); hhi = warp_sum(hhi); nlo = warp_sum(nlo); nhi = warp_sum(nhi);
@@ -191,8 +215,9 @@ GraphTotals validate_graph(gp_ctx *ctx, const DevGraph &g, bool full) {
   GP_REQUIRE(!(h.err & VE_XADJ), GP_ERR_INVALID, "xadj is not a valid row-offset array");
   GP_REQUIRE(!(h.err & VE_VWGT), GP_ERR_INVALID, "node weights must be > 0");
   GP_REQUIRE(h.csum <= 0x7FFFFFFFull, GP_ERR_OVERFLOW, "total node weight exceeds 2^31 - 1");
+  prof_bytes(ctx, PROF_VALIDATE, 8.0 * g.n + 8.0 * g.m2);  // offsets, node weights, ids, edge weights
   if (g.m2 > 0) {
-    k_validate_entries<<<grid_for((g.m2 + 1023) / 1024 * 32, 256, ctx->num_sms * 16), 256, 0, ctx->stream>>>(
+    k_validate_entries<<<grid_for(g.n, 256, ctx->num_sms * 16), 256, 0, ctx->stream>>>(
         g.xadj, g.adjncy, g.adjwgt, g.n, g.m2, o.get());
     GP_LAUNCH_CHECK();
     read_back(ctx, o.get(), sizeof(ValOut), &h);
@@ -212,6 +237,7 @@ void project(gp_ctx *ctx, int32_t n, const int32_t *cmap, const int32_t *coarse,
   if (n <= 0) return;
   k_project<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(n, cmap, coarse, fine);
   GP_LAUNCH_CHECK();
+  prof_bytes(ctx, PROF_PROJECT, 12.0 * n);  // coarse id read, coarse block gathered, fine block written
 }
 
 void cut_and_weights(gp_ctx *ctx, const DevGraph &g, const int32_t *blocks, int32_t k, int64_t *cut_host,
@@ -232,6 +258,9 @@ void cut_and_weights(gp_ctx *ctx, const DevGraph &g, const int32_t *blocks, int3
       GP_LAUNCH_CHECK();
     }
   }
+  // per entry: neighbour id, weight, neighbour block; per node: row offset, own block
+  const double bb = k <= 255 ? 1.0 : 4.0;
+  prof_bytes(ctx, PROF_CUT, (8.0 + bb) * g.m2 + (4.0 + bb) * g.n);
   if (bw_host) {
     DBuf<unsigned long long> bw(ctx, (size_t)k);
     block_weights_dev(ctx, g, blocks, k, bw.get());
@@ -260,7 +289,7 @@ int64_t refine_blocks(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t Lmax, i
     k_narrow<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(blocks, g.n, b8.get());
     GP_LAUNCH_CHECK();
   }
-  LpResult r = lp_run(ctx, g, blocks, bw.get(), nullptr, k, seed, p, nullptr, b8.get());
+  LpResult r = lp_run(ctx, g, blocks, bw.get(), k, seed, p, nullptr, b8.get());
   return r.moves;
 }
 

@@ -12,9 +12,11 @@
 // its hash is below floor(m_hat 2^32 / m).  Both CSR directions of an edge
 // see the same hash, so the result stays symmetric.
 //
-// Keep decisions are packed into one bit per entry (a 32-entry word per warp
-// step), a prefix sum over word counts gives every kept entry its position,
-// and the kept entries are compacted in one flat pass.
+// Two passes over the entries, each warp walking 32 consecutive rows (one
+// contiguous range of entries): the first counts the kept entries of every
+// row, a prefix sum turns the counts into the new row offsets, and the second
+// takes the same keep decisions again and writes the kept entries of the 32
+// rows contiguously from the first row's new offset.
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -50,83 +52,82 @@ __global__ void k_whist(const int32_t *__restrict__ w, int64_t m2, int cap_mode,
 struct KeepArgs {
   const int32_t *xadj, *adjncy, *adjwgt;
   int n;
-  int64_t m2;
   int mode;  // 0 keep none, 1 threshold, 2 uniform, 3 keep all
   int32_t wt;
   uint64_t T;
   uint64_t key;
-  uint32_t *words;
-  int32_t *wcnt;
+  int32_t *cnt;         // count pass: kept entries per row
+  const int32_t *nxadj; // write pass: new row offsets
+  int32_t *oadj, *ow;
 };
 
-constexpr int kWordsPerChunk = 32;
+constexpr int kKeepUnroll = 4;
 
-__global__ void __launch_bounds__(256) k_keep_bits(KeepArgs a) {
-  const int lane = (int)lane_id();
-  const int64_t nwords = (a.m2 + 31) / 32;
-  const int64_t nchunks = (nwords + kWordsPerChunk - 1) / kWordsPerChunk;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = wid; c < nchunks; c += nw) {
-    const int64_t w0 = c * kWordsPerChunk;
-    const int64_t w1 = w0 + kWordsPerChunk < nwords ? w0 + kWordsPerChunk : nwords;
-    int row = 0;
-    if (lane == 0) row = row_of(a.xadj, a.n, w0 * 32);
-    row = __shfl_sync(FULL, row, 0);
-    for (int64_t wi = w0; wi < w1; wi++) {
-      const int64_t e = wi * 32 + lane;
-      bool keep = false;
-      if (e < a.m2) {
-        while (row < a.n - 1 && (int64_t)a.xadj[row + 1] <= e) row++;
-        if (a.mode == 3) {
-          keep = true;
-        } else if (a.mode != 0) {
-          const int v = a.adjncy[e];
-          const uint32_t lo = (uint32_t)(row < v ? row : v), hi = (uint32_t)(row < v ? v : row);
-          const uint64_t h = h32(a.key, lo, hi);
-          if (a.mode == 2) {
-            keep = h < a.T;
-          } else {
-            const int x = a.adjwgt[e];
-            keep = x > a.wt || (x == a.wt && h < a.T);
+__device__ __forceinline__ bool keep_entry(const KeepArgs &a, int row, int v, int x) {
+  if (a.mode == 3) return true;
+  if (a.mode == 0) return false;
+  const uint32_t lo = (uint32_t)(row < v ? row : v), hi = (uint32_t)(row < v ? v : row);
+  const uint64_t h = h32(a.key, lo, hi);
+  if (a.mode == 2) return h < a.T;
+  return x > a.wt || (x == a.wt && h < a.T);
+}
+
+// WRITE = false: kept entries per row; WRITE = true: the kept entries, compacted.
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_keep(KeepArgs a) {
+  __shared__ int s_cnt[8][32];
+  const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int64_t u0 = (int64_t)wid * 32; u0 < a.n; u0 += (int64_t)nw * 32) {
+    const int64_t u = u0 + lane;
+    const bool valid = u < a.n;
+    const int xe = valid ? a.xadj[u + 1] : 0x7FFFFFFF;
+    const int e0 = a.xadj[u0];
+    const int last = (int)((a.n - u0) < 32 ? (a.n - u0) : 32) - 1;
+    const int e1 = __shfl_sync(FULL, xe, last);
+    if (!WRITE) s_cnt[wib][lane] = 0;
+    int out = WRITE ? a.nxadj[u0] : 0;
+    __syncwarp();
+    for (int f0 = e0; f0 < e1; f0 += 32 * kKeepUnroll) {
+      int e[kKeepUnroll], j[kKeepUnroll], v[kKeepUnroll], x[kKeepUnroll];
+#pragma unroll
+      for (int r = 0; r < kKeepUnroll; r++) {
+        e[r] = f0 + r * 32 + lane;
+        int q = 0;  // owner: lanes whose row ends at or before e
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int val = __shfl_sync(FULL, xe, q + step - 1);
+          if (val <= e[r]) q += step;
+        }
+        j[r] = q;
+      }
+#pragma unroll
+      for (int r = 0; r < kKeepUnroll; r++) {
+        v[r] = e[r] < e1 ? a.adjncy[e[r]] : 0;
+        x[r] = e[r] < e1 ? a.adjwgt[e[r]] : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < kKeepUnroll; r++) {
+        const bool k = e[r] < e1 && keep_entry(a, (int)(u0 + j[r]), v[r], x[r]);
+        if (WRITE) {
+          const unsigned m = __ballot_sync(FULL, k);
+          if (k) {
+            const int pos = out + __popc(m & lanemask_lt());
+            a.oadj[pos] = v[r];
+            a.ow[pos] = x[r];
           }
+          out += __popc(m);
+        } else if (k) {
+          atomicAdd(&s_cnt[wib][j[r]], 1);
         }
       }
-      const unsigned m = __ballot_sync(FULL, keep);
-      if (lane == 0) {
-        a.words[wi] = m;
-        a.wcnt[wi] = __popc(m);
-      }
     }
-  }
-}
-
-__global__ void k_new_xadj(const int32_t *xadj, int n, int64_t m2, const uint32_t *words,
-                           const int32_t *woff, int32_t total, int32_t *out) {
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = xadj[r];
-    if (e >= m2) { out[r] = total; continue; }
-    const int64_t wi = e >> 5;
-    const unsigned b = (unsigned)(e & 31);
-    out[r] = woff[wi] + __popc(words[wi] & ((1u << b) - 1u));
-  }
-}
-
-__global__ void __launch_bounds__(256) k_compact(const int32_t *adjncy, const int32_t *adjwgt, int64_t m2,
-                                                 const uint32_t *words, const int32_t *woff,
-                                                 int32_t *oadj, int32_t *ow) {
-  const int lane = (int)lane_id();
-  const int64_t nwords = (m2 + 31) / 32;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t wi = wid; wi < nwords; wi += nw) {
-    const unsigned m = words[wi];
-    if (!((m >> lane) & 1u)) continue;
-    const int64_t e = wi * 32 + lane;
-    const int pos = woff[wi] + __popc(m & lanemask_lt());
-    oadj[pos] = adjncy[e];
-    ow[pos] = adjwgt[e];
+    if (!WRITE) {
+      __syncwarp();
+      if (valid) a.cnt[u] = s_cnt[wib][lane];
+      __syncwarp();
+    }
   }
 }
 
@@ -208,29 +209,37 @@ void sparsify_graph(gp_ctx *ctx, const DevGraph &g, int64_t m_hat, int32_t level
   }
   const uint64_t key = stream_key(seed, mode == GP_SPARSIFY_UNIFORM ? TAG_UNIFORM : TAG_SPARSE,
                                   (uint32_t)level, 0);
-  const int64_t nwords = (m2 + 31) / 32;
-  DBuf<uint32_t> words(ctx, (size_t)(nwords > 0 ? nwords : 1));
-  DBuf<int32_t> wcnt(ctx, (size_t)(nwords > 0 ? nwords : 1)), woff(ctx, (size_t)(nwords > 0 ? nwords : 1));
-  DBuf<int32_t> total(ctx, 1);
-  if (nwords > 0) {
-    KeepArgs a{g.xadj, g.adjncy, g.adjwgt, n, m2, kmode, wt, T, key, words.get(), wcnt.get()};
-    const int64_t chunks = (nwords + kWordsPerChunk - 1) / kWordsPerChunk;
-    k_keep_bits<<<grid_for(chunks * 32, 256, ctx->num_sms * 16), 256, 0, ctx->stream>>>(a);
+  KeepArgs a{g.xadj, g.adjncy, g.adjwgt, n, kmode, wt, T, key, nullptr, nullptr, nullptr, nullptr};
+  DBuf<int32_t> cnt(ctx, (size_t)n + 1), total(ctx, 1);
+  const int kgrid = grid_for(n, 256, ctx->num_sms * 16);
+  GP_CUDA(cudaMemsetAsync(cnt.get() + n, 0, sizeof(int32_t), ctx->stream));
+  if (n > 0) {
+    a.cnt = cnt.get();
+    k_keep<false><<<kgrid, 256, 0, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
   }
-  scan_exclusive_i32(ctx, wcnt.get(), woff.get(), nwords, total.get());
+  out.n = n;
+  out.bx.reset(ctx, (size_t)n + 1);
+  out.xadj = out.bx.get();
+  scan_exclusive_i32(ctx, cnt.get(), out.xadj, n + 1, total.get());
   const int32_t m2_out = read_scalar(ctx, total.get());
-  out.allocate(ctx, n, m2_out);
-  k_new_xadj<<<grid_for((int64_t)n + 1, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(
-      g.xadj, n, m2, words.get(), woff.get(), m2_out, out.xadj);
-  GP_LAUNCH_CHECK();
-  if (nwords > 0) {
-    k_compact<<<grid_for(nwords * 32, 256, ctx->num_sms * 16), 256, 0, ctx->stream>>>(
-        g.adjncy, g.adjwgt, m2, words.get(), woff.get(), out.adjncy, out.adjwgt);
+  out.m2 = m2_out;
+  out.ba.reset(ctx, (size_t)m2_out);
+  out.bw.reset(ctx, (size_t)m2_out);
+  out.adjncy = out.ba.get();
+  out.adjwgt = out.bw.get();
+  out.bv.reset(ctx, (size_t)n);
+  out.vwgt = out.bv.get();
+  if (n > 0 && m2_out > 0) {
+    a.nxadj = out.xadj; a.oadj = out.adjncy; a.ow = out.adjwgt;
+    k_keep<true><<<kgrid, 256, 0, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
   }
   if (n > 0)
     GP_CUDA(cudaMemcpyAsync(out.vwgt, g.vwgt, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  // weights once for the selection (T-Weight only), ids and weights once for the keep test,
+  // the kept entries written, row offsets read and written, node weights copied
+  prof_bytes(ctx, PROF_SPARSIFY, (kmode == 1 ? 4.0 * m2 : 0.0) + 8.0 * m2 + 8.0 * m2_out + 8.0 * (n + 1) + 8.0 * n);
   if (trace.on())
     fprintf(stderr, "[gp sparsify] m2=%lld -> %d ms=%.2f\n", (long long)m2, m2_out, trace.ms());
   if (st) {
