@@ -98,6 +98,26 @@ def traffic_ratio(cls):
     return d["dram_bytes"] / d["algorithmic_bytes"], d["capture"]
 
 
+def gather_floor(ctx, st, rates):
+    """Lower bound (ms per step) of the label reads of the clustering LP and of the
+    coarse-id reads of contraction: per level, the rated entries (every node with
+    neighbours is rated once per round of 8 sub-rounds) and the contracted entries,
+    each a random 4-byte read from an n_i-word array, at the measured random-read
+    rate for that array size."""
+    def rate(n):
+        b = max(4, 4 * int(n))
+        if b not in rates:
+            rates[b] = ctx.measure_random_reads(b, 1 << 26)
+        return rates[b]
+    lp = contract = 0.0
+    for L in st.levels_list():
+        entries = 2 * L["m"]
+        r = rate(L["n"])
+        lp += entries * L["lp_subrounds"] / 8.0 / r
+        contract += entries / r
+    return 1000 * lp, 1000 * contract
+
+
 # ------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -313,6 +333,17 @@ def run_gpu(args, world, rank, local):
                             "ms": v["ms"], "launches": v["launches"]}
                         for k, v in prof.items() if v["bytes"] > 0 and v["ms"] > 0}}
 
+    # the random-read bound of the gather-heavy classes (measured on this GPU, per level)
+    rates = {}
+    lp_floor, ct_floor = gather_floor(ctx, st, rates)
+    per_step = lambda k: prof[k]["ms"] / args.steps
+    roof["random_read_bound"] = {
+        "what": "time the label / coarse-id reads alone take at the measured random 4-byte read rate "
+                "for each level's array size (entries rated per level = 2m x sub-rounds / 8)",
+        "lp_rate": {"floor_ms": lp_floor, "ms": per_step("lp_rate"), "frac": lp_floor / per_step("lp_rate")},
+        "contract": {"floor_ms": ct_floor, "ms": per_step("contract"), "frac": ct_floor / per_step("contract")},
+        "reads_per_s_by_array_bytes": {str(k): v for k, v in sorted(rates.items())}}
+
     # end to end through the host entry point from pinned memory
     e2e = None
     if not args.no_e2e:
@@ -368,6 +399,52 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+def run_level1(args):
+    """Level 1 of Alg. 1 alone (LP clustering with 2-hop and isolated nodes, contraction, and
+    sparsification when it triggers) on the workload graph: the profiling case for ncu."""
+    import torch
+    import paper_2504_17615_gb300 as gp
+    from paper_2504_17615_gb300 import build as gpbuild
+    w = workload_of(args)
+    gpbuild.build()
+    g = make_graph(w, 0, 1)
+    ctx = gp.Context(0)
+    dg = gp.DeviceGraph.from_host(g)
+    U = max(1, g.n // (160 * w["k"]))
+    m = g.m2 // 2
+
+    def step():
+        cmap, nc, _ = ctx.gp_coarsen(dg, U, 1, w["seed"])
+        cg = ctx.gp_contract(dg, cmap, nc)
+        m_c = cg.m2 // 2
+        m_hat = min(m // 2, (m * nc) // (2 * g.n))  # tau_e = tau_d = 1/2
+        if m_c > 4 * m_hat:  # rho = 4
+            sg, _ = ctx.gp_sparsify(cg, m_hat, 2, w["seed"])
+            sg.release()
+        cg.release()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_reset()
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(ctx.stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    print(json.dumps({"metric": "level-1 edges/s (clustering, contraction, sparsification)",
+                      "value": m / (ms / 1000.0), "unit": "edges/s", "ms_per_step": ms, "steps": args.steps,
+                      "warmup": args.warmup, "config": {"workload": w["name"], "U": U},
+                      "kernel_classes": {k: v for k, v in prof.items() if v["launches"]}}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,6 +456,8 @@ def main():
                     help="ER graph with 2^S nodes and average degree 20 instead (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--level1", action="store_true",
+                    help="time level 1 of Alg. 1 alone on the workload graph (profiling case)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()
@@ -387,6 +466,8 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.level1:
+        return run_level1(args)
     return run_gpu(args, world, rank, local)
 
 

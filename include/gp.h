@@ -254,15 +254,27 @@ void gp_graph_release(gp_ctx *ctx, gp_graph *g);
 /*
  * Profiling: when enabled, every major kernel launch is bracketed by CUDA
  * events on the context stream, and gp_profile_read returns, per kernel
- * class, the launch count, the summed device time (ms) and the algorithmic
- * bytes moved (the per-unit figures of the design document).  Classes are
- * named by gp_profile_name(i) for i < gp_profile_count().
+ * class, the number of bracketed launch groups, the summed device time (ms)
+ * and the algorithmic bytes moved: the bytes the step must read and write
+ * at least (each CSR entry, label, weight and output word counted once, at
+ * its own width), from unit counts the kernels record.  Classes are named by
+ * gp_profile_name(i) for i < gp_profile_count().
  */
 void gp_profile_enable(gp_ctx *ctx, int on);
 void gp_profile_reset(gp_ctx *ctx);
 int gp_profile_count(void);
 const char *gp_profile_name(int i);
 gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, double *bytes);
+
+/*
+ * Measurement helper with no counterpart in the paper: the device's rate of
+ * random 4-byte reads from an array of `array_bytes` bytes (`reads` reads,
+ * indices from a counter hash, timed with CUDA events after two warm-up
+ * passes).  The label and coarse-id reads of the rating and contraction
+ * kernels are such reads, so this rate bounds them.  Allocates the array
+ * through the context allocator; returns reads per second in *reads_per_s.
+ */
+gp_status gp_measure_random_reads(gp_ctx *ctx, int64_t array_bytes, int64_t reads, double *reads_per_s);
 
 #ifdef __cplusplus
 }

@@ -128,6 +128,7 @@ def _load():
             "gp_profile_name": (ctypes.c_char_p, [ctypes.c_int]),
             "gp_profile_read": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(d),
                                                ctypes.POINTER(d)]),
+            "gp_measure_random_reads": (ctypes.c_int, [P, i64, i64, ctypes.POINTER(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -252,9 +253,11 @@ class LibGraph:
 # -------------------------------------------------------------- context
 
 class Context:
-    """A library context on one device and stream, allocating through torch."""
+    """A library context on one device and stream.  Device memory comes from the
+    library's own stream-ordered pool, or from torch's caching allocator when
+    use_torch_allocator is set (one Python call per allocation: slower)."""
 
-    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device available: the partitioner runs on the GPU only")
@@ -421,6 +424,12 @@ class Context:
             out[self.lib.gp_profile_name(i).decode()] = {"launches": la.value, "ms": ms.value,
                                                          "bytes": by.value}
         return out
+
+    def measure_random_reads(self, array_bytes: int, reads: int) -> float:
+        """Random 4-byte reads per second from an array of array_bytes bytes."""
+        r = ctypes.c_double(0)
+        self._check(self.lib.gp_measure_random_reads(self.ptr, array_bytes, reads, ctypes.byref(r)))
+        return r.value
 
 
 def version() -> str:

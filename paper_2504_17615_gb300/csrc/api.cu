@@ -92,6 +92,17 @@ gp_status gp_create(gp_ctx **out, int device, void *stream, const gp_allocator *
     GP_CUDA(cudaSetDevice(device));
     GP_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
     GP_CUDA(cudaMallocHost((void **)&ctx->h_stage, 4096 * sizeof(int64_t)));
+    if (!ctx->alloc.alloc) {
+      // a private pool that keeps freed memory for reuse: allocations in the level loop
+      // then cost no driver call
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      GP_CUDA(cudaMemPoolCreate(&ctx->pool, &props));
+      uint64_t keep = UINT64_MAX;
+      GP_CUDA(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     void *p = nullptr;
     GP_CUDA(cudaMalloc(&p, sizeof(unsigned long long) * gp::PROF_COUNT_ * gp::PROF_UNITS));
     ctx->d_units = (unsigned long long *)p;
@@ -116,6 +127,7 @@ void gp_destroy(gp_ctx *ctx) {
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->d_units) cudaFree(ctx->d_units);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // released once its last allocation is freed
   delete ctx;
 }
 
@@ -311,15 +323,16 @@ gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, dou
     unsigned long long u[gp::PROF_UNITS] = {};
     if (ctx->d_units)
       gp::read_back(ctx, ctx->d_units + (size_t)i * gp::PROF_UNITS, sizeof(u), u);
-    // algorithmic bytes per unit (see the design document, kernel table)
+    // algorithmic bytes: each unit at its own width, counted once
     double b = 0;
     switch (i) {
       case gp::PROF_LP_RATE:
       case gp::PROF_REF_RATE:
-        // per entry: neighbour id, edge weight, neighbour label (12 B); per candidate
-        // label its weight (4 B); per node offsets, weight, own label (16 B); per
-        // proposal target write + incoming update (12 B)
-        b = 12.0 * u[0] + 4.0 * u[2] + 16.0 * u[1] + 12.0 * u[3];
+        // per entry: neighbour id, edge weight, neighbour label (12 B, 9 B when the
+        // labels are one byte); per candidate label its weight (4 B); per node
+        // offsets, weight, own label (16 B); per proposal target write + incoming
+        // update (12 B)
+        b = 12.0 * u[0] - 3.0 * u[4] + 4.0 * u[2] + 16.0 * u[1] + 12.0 * u[3];
         break;
       case gp::PROF_CONTRACT:
         // map: per fine entry neighbour id, weight, coarse id of the neighbour read (12 B) and
@@ -333,6 +346,13 @@ gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, dou
     if (launches) *launches = ctx->prof_launches[i];
     if (ms) *ms = ctx->prof_ms[i];
     if (bytes) *bytes = b;
+  });
+}
+
+gp_status gp_measure_random_reads(gp_ctx *ctx, int64_t array_bytes, int64_t reads, double *reads_per_s) {
+  return guarded(ctx, [&] {
+    GP_REQUIRE(reads_per_s, GP_ERR_INVALID, "null output");
+    *reads_per_s = gp::measure_random_reads(ctx, array_bytes, reads);
   });
 }
 

@@ -75,8 +75,9 @@ enum ProfClass {
   PROF_COUNT_
 };
 
-// device-side unit counters, per class: [0] entries, [1] vertices, [2] candidates, [3] proposals
-constexpr int PROF_UNITS = 4;
+// device-side unit counters, per class: [0] entries, [1] vertices, [2] candidates, [3] proposals,
+// [4] entries whose neighbour label was read as one byte
+constexpr int PROF_UNITS = 5;
 
 struct ProfRecord {
   int cls;
@@ -92,6 +93,7 @@ struct gp_ctx {
   cudaStream_t stream = nullptr;
   gp_allocator alloc{};
   bool own_alloc = false;
+  cudaMemPool_t pool = nullptr;  // the library's own stream-ordered pool (no external allocator)
   int num_sms = 0;
   std::string last_error;
   // small pinned host staging area and device scratch for counters
@@ -393,6 +395,7 @@ struct GraphTotals {
 };
 GraphTotals validate_graph(gp_ctx *ctx, const DevGraph &g, bool full);
 int64_t lmax_of(int64_t W, int32_t k, int64_t eps_ppm);
+double measure_random_reads(gp_ctx *ctx, int64_t array_bytes, int64_t reads);
 void check_blocks(gp_ctx *ctx, const int32_t *blocks, int n, int k);
 void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, uint64_t seed,
                     const gp_config &cfg, int32_t *blocks, int64_t *cut_out, gp_partition_stats *st);

@@ -17,6 +17,8 @@
 //            when that count reaches n_min or a round moved nothing.
 #include "lp.cuh"
 
+#include <chrono>
+
 namespace gp {
 
 namespace {
@@ -46,11 +48,12 @@ struct RateArgs {
 
 __device__ __forceinline__ void add_units(unsigned long long *units, unsigned long long e,
                                           unsigned long long v, unsigned long long c,
-                                          unsigned long long p) {
+                                          unsigned long long p, bool narrow) {
   if (!units) return;
   e = warp_sum(e); v = warp_sum(v); c = warp_sum(c); p = warp_sum(p);
   if (lane_id() == 0) {
     if (e) atomicAdd(units + 0, e);
+    if (e && narrow) atomicAdd(units + 4, e);
     if (v) atomicAdd(units + 1, v);
     if (c) atomicAdd(units + 2, c);
     if (p) atomicAdd(units + 3, p);
@@ -194,14 +197,18 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
         own_r[q] = __reduce_max_sync(gmask, (lead[q] && L[q] == own[q]) ? sum[q] : 0);
     }
     // choose: all U sets advance together, so that the weight reads of their
-    // leading candidates are issued side by side
-    bool alive[U], searching[U];
+    // leading candidates are issued side by side.  When a group's leading
+    // candidate does not fit, the weights of all its remaining candidates are
+    // read at once on the next pass and the inadmissible ones dropped, so a
+    // node takes at most three passes.
+    bool alive[U], searching[U], eager[U];
     unsigned best[U];
 #pragma unroll
     for (int q = 0; q < U; q++) {
       alive[q] = lead[q] && L[q] != own[q];
       uc += alive[q];
       searching[q] = v[q] >= 0;
+      eager[q] = false;
       best[q] = 0xFFFFFFFFu;
     }
     for (int it = 0; it <= G; it++) {  // bounded: every pass drops one candidate per searching group
@@ -209,6 +216,14 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
 #pragma unroll
       for (int q = 0; q < U; q++) any = any || searching[q];
       if (!__any_sync(FULL, any)) break;
+      if (MODE == RATE_LP) {
+        int we[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) we[q] = (eager[q] && searching[q] && alive[q]) ? a.weight[L[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < U; q++)
+          if (eager[q] && searching[q] && alive[q] && (int64_t)we[q] + cv[q] > a.bound) alive[q] = false;
+      }
       unsigned c[U];
       bool holder[U];
 #pragma unroll
@@ -228,12 +243,14 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
       } else {
         int wc[U];
 #pragma unroll
-        for (int q = 0; q < U; q++) wc[q] = holder[q] ? a.weight[c[q]] : 0;
+        for (int q = 0; q < U; q++) wc[q] = (holder[q] && !eager[q]) ? a.weight[c[q]] : 0;
 #pragma unroll
         for (int q = 0; q < U; q++) {
-          const unsigned fits = holder[q] && (int64_t)wc[q] + cv[q] <= a.bound ? 1u : 0u;
+          // after an eager pass every remaining candidate fits
+          const unsigned fits = holder[q] && (eager[q] || (int64_t)wc[q] + cv[q] <= a.bound) ? 1u : 0u;
           if (__reduce_or_sync(gmask, fits) && searching[q]) { best[q] = c[q]; searching[q] = false; }
           alive[q] = alive[q] && (unsigned)L[q] != c[q];
+          eager[q] = true;
         }
       }
     }
@@ -249,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
       }
     }
   }
-  add_units(a.units, ue, uv, uc, up);
+  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr);
 }
 
 // --------------------------------------- degree <= 128: warp/node + table
@@ -312,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
     for (int t = lane; t < kMedSlots; t += 32) { tk[t] = -1; tv[t] = 0; }
     __syncwarp();
   }
-  add_units(a.units, ue * (lane == 0), uv * (lane == 0), uc, up);
+  add_units(a.units, ue * (lane == 0), uv * (lane == 0), uc, up, a.label8 != nullptr);
 }
 
 // --------------------------------------------- degree > 128: block/node
@@ -405,7 +422,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
     for (int t = threadIdx.x; t < tsize; t += blockDim.x) { tk[t] = -1; tv[t] = 0; }
     __syncthreads();
   }
-  add_units(a.units, ue, uv, uc, up);
+  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr);
 }
 
 // ----------------------------------------------------- per-round buckets
@@ -603,6 +620,87 @@ __global__ void k_ov_accept(const uint64_t *keys, const uint32_t *vals, int n, c
   }
 }
 
+// ------------------------------------------ small overflow sets
+//
+// Up to kOvSmall proposers of overflowing targets are ordered by (target,
+// priority, node) with a bitonic sort in one block's shared memory; a block
+// scan of their weights gives every proposer its running weight within its
+// target, and it is accepted iff the target's weight plus that fits.
+
+constexpr int kOvSmall = 2048;
+constexpr int kOvSmallThreads = 1024;
+
+__global__ void __launch_bounds__(kOvSmallThreads) k_ov_small(uint64_t *key, uint32_t *val, int nov,
+                                                              const int32_t *vwgt, const int32_t *weight,
+                                                              int64_t bound, uint8_t *acc) {
+  __shared__ uint64_t s_k[kOvSmall];
+  __shared__ uint32_t s_v[kOvSmall];
+  __shared__ long long s_w[kOvSmallThreads / 32];
+  int P = 1;
+  while (P < nov) P <<= 1;
+  const int t = threadIdx.x;
+  for (int i = t; i < P; i += blockDim.x) {
+    s_k[i] = i < nov ? key[i] : ~0ull;
+    s_v[i] = i < nov ? val[i] : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = t; i < P / 2; i += blockDim.x) {
+        const int lo = 2 * i - (i & (stride - 1));  // pairs (lo, lo + stride)
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t ka = s_k[lo], kb = s_k[hi];
+        const uint32_t va = s_v[lo], vb = s_v[hi];
+        const bool gt = ka > kb || (ka == kb && va > vb);
+        if (gt == up) { s_k[lo] = kb; s_k[hi] = ka; s_v[lo] = vb; s_v[hi] = va; }
+      }
+      __syncthreads();
+    }
+  }
+  // sorted order written back; inclusive running weights (their total is at most
+  // the graph's node weight, below 2^31) replace the node ids in shared memory
+  long long carry = 0;
+  const int lane = (int)lane_id(), wp = t >> 5, nwp = blockDim.x >> 5;
+  for (int c0 = 0; c0 < nov; c0 += blockDim.x) {
+    const int i = c0 + t;
+    long long x = 0;
+    if (i < nov) {
+      const uint32_t v = s_v[i];
+      key[i] = s_k[i];
+      val[i] = v;
+      x = vwgt[v];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[wp] = x;
+    __syncthreads();
+    long long before = carry, chunk = 0;
+    for (int q = 0; q < nwp; q++) {
+      if (q < wp) before += s_w[q];
+      chunk += s_w[q];
+    }
+    if (i < nov) s_v[i] = (uint32_t)(before + x);
+    carry += chunk;
+    __syncthreads();
+  }
+  for (int i = t; i < nov; i += blockDim.x) {
+    // first proposer of i's target: lower bound of (target << 32) in the sorted keys
+    const uint64_t seg = s_k[i] & 0xFFFFFFFF00000000ull;
+    int a = 0, b = i;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (s_k[mid] < seg) a = mid + 1; else b = mid;
+    }
+    const long long incl = (long long)s_v[i] - (a > 0 ? (long long)s_v[a - 1] : 0);
+    const int K = (int)(s_k[i] >> 32);
+    acc[i] = (int64_t)weight[K] + incl <= bound ? 1 : 0;
+  }
+}
+
 // ------------------------------------------ overflow with few labels
 //
 // The proposers of overflowing targets are not sorted.  Per target, a
@@ -784,47 +882,59 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
     atomicAdd((unsigned long long *)&a.cnt->moved_sub, (unsigned long long)moved);
 }
 
-// Clears the incoming weights of the sub-round's targets.
-__global__ void __launch_bounds__(kThreads) k_finalize(ApplyArgs a) {
+// Closes a sub-round in one launch: clears the incoming weights of its
+// targets, counts the non-empty clusters (node weights are positive, so a
+// label is in use iff its weight is), and the last block to finish updates
+// the counters: cluster count, moves, the stop flag (cluster count at n_min;
+// at the end of a round, a round without moves), and clears the proposal
+// list sizes for the next sub-round.
+__global__ void __launch_bounds__(kThreads) k_close(ApplyArgs a, int64_t count_labels, long long n_min,
+                                                    int round_end, unsigned *done) {
+  Counters *cnt = a.cnt;
+  if (cnt->stop) return;
   const int total = a.nmov + a.nov;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int K = t < a.nmov ? a.mov_k[t] : (int)(a.ov_key[t - a.nmov] >> 32);
     a.incoming[K] = 0;
   }
-}
-
-// Non-empty clusters: node weights are positive, so a label is in use iff its weight is.
-__global__ void __launch_bounds__(kThreads) k_count_nonempty(const int32_t *weight, int64_t nlabels,
-                                                             Counters *cnt) {
-  if (cnt->stop) return;
-  long long c = 0;
-  const int4 *w4 = reinterpret_cast<const int4 *>(weight);
-  const int64_t n4 = nlabels / 4;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-    const int4 x = w4[i];
-    c += (x.x > 0) + (x.y > 0) + (x.z > 0) + (x.w > 0);
+  if (count_labels > 0) {
+    long long c = 0;
+    const int4 *w4 = reinterpret_cast<const int4 *>(a.weight);
+    const int64_t n4 = count_labels / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+      const int4 x = w4[i];
+      c += (x.x > 0) + (x.y > 0) + (x.z > 0) + (x.w > 0);
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count_labels;
+         i += (int64_t)gridDim.x * blockDim.x)
+      c += a.weight[i] > 0;
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd((unsigned long long *)&cnt->nonempty, (unsigned long long)c);
   }
-  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nlabels;
-       i += (int64_t)gridDim.x * blockDim.x)
-    c += weight[i] > 0;
-  c = warp_sum(c);
-  if (lane_id() == 0 && c) atomicAdd((unsigned long long *)&cnt->nonempty, (unsigned long long)c);
-}
-
-__global__ void k_subround_end(Counters *cnt, int count_clusters, long long n_min) {
-  if (cnt->stop) return;
-  if (count_clusters) cnt->nclusters = cnt->nonempty;
-  cnt->nonempty = 0;
-  cnt->moved_round += cnt->moved_sub;
-  cnt->moved_total += cnt->moved_sub;
-  cnt->moved_sub = 0;
-  if (count_clusters && cnt->nclusters <= n_min) cnt->stop = 1;
-}
-
-__global__ void k_round_end(Counters *cnt) {
-  if (cnt->stop) return;
-  if (cnt->moved_round == 0) cnt->stop = 1;
-  cnt->moved_round = 0;
+  __syncthreads();
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  volatile Counters *vc = cnt;
+  if (count_labels > 0) vc->nclusters = vc->nonempty;
+  vc->nonempty = 0;
+  const long long moved = vc->moved_sub;
+  vc->moved_round = vc->moved_round + moved;
+  vc->moved_total = vc->moved_total + moved;
+  vc->moved_sub = 0;
+  vc->nov = 0;
+  vc->nmov = 0;
+  if (count_labels > 0 && vc->nclusters <= n_min) vc->stop = 1;
+  if (round_end) {
+    if (!vc->stop && vc->moved_round == 0) vc->stop = 1;
+    vc->moved_round = 0;
+  }
+  *done = 0;
 }
 
 __global__ void k_counters_init(Counters *cnt, long long nclusters) {
@@ -832,7 +942,6 @@ __global__ void k_counters_init(Counters *cnt, long long nclusters) {
   cnt->moved_total = 0; cnt->nonempty = 0; cnt->nclusters = nclusters;
 }
 
-__global__ void k_reset_lists(Counters *cnt) { cnt->nov = 0; cnt->nmov = 0; }
 
 __global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -878,38 +987,64 @@ void make_tables(gp_ctx *ctx, const DevGraph &g, RateTables &t) {
   }
 }
 
+// Grid for `count` listed nodes, `per_block` nodes per block and iteration
+// (count < 0: unknown, the full grid).
+inline int rate_grid(gp_ctx *ctx, int64_t count, int per_block, int cap) {
+  if (count < 0) return cap;
+  return grid_for(count, per_block, cap);
+}
+
+template <int G, int U>
+constexpr int group_nodes_per_block() { return kWarpsPerBlock * (32 / G) * U; }
+
+// hcnt: the five bucket sizes of this sub-round when the host knows them (empty
+// buckets are then not launched), else nullptr
 template <int MODE, int LK>
-void launch_groups(gp_ctx *ctx, const RateArgs &a0, int bucket_key_base) {
-  const int grid_w = ctx->num_sms * 8;
+void launch_groups(gp_ctx *ctx, const RateArgs &a0, int bucket_key_base, const int *hcnt) {
+  const int cap = ctx->num_sms * 8;
   RateArgs a = a0;
-  a.key = bucket_key_base + 0;
-  k_rate_group<MODE, 8, 2, LK><<<grid_w, kThreads, 0, ctx->stream>>>(a);
-  GP_LAUNCH_CHECK();
-  a.key = bucket_key_base + 1;
-  k_rate_group<MODE, 16, 2, LK><<<grid_w, kThreads, 0, ctx->stream>>>(a);
-  GP_LAUNCH_CHECK();
-  a.key = bucket_key_base + 2;
-  k_rate_group<MODE, 32, 4, LK><<<grid_w, kThreads, 0, ctx->stream>>>(a);
-  GP_LAUNCH_CHECK();
+  if (!hcnt || hcnt[0] > 0) {
+    a.key = bucket_key_base + 0;
+    k_rate_group<MODE, 8, 2, LK><<<rate_grid(ctx, hcnt ? hcnt[0] : -1, group_nodes_per_block<8, 2>(), cap),
+                                   kThreads, 0, ctx->stream>>>(a);
+    GP_LAUNCH_CHECK();
+  }
+  if (!hcnt || hcnt[1] > 0) {
+    a.key = bucket_key_base + 1;
+    k_rate_group<MODE, 16, 2, LK><<<rate_grid(ctx, hcnt ? hcnt[1] : -1, group_nodes_per_block<16, 2>(), cap),
+                                    kThreads, 0, ctx->stream>>>(a);
+    GP_LAUNCH_CHECK();
+  }
+  if (!hcnt || hcnt[2] > 0) {
+    a.key = bucket_key_base + 2;
+    k_rate_group<MODE, 32, 4, LK><<<rate_grid(ctx, hcnt ? hcnt[2] : -1, group_nodes_per_block<32, 4>(), cap),
+                                    kThreads, 0, ctx->stream>>>(a);
+    GP_LAUNCH_CHECK();
+  }
 }
 
 // nlabels: number of labels (chooses the narrow / dense group kernels when
 // a uint8 copy of the labels is present)
 template <int MODE>
-void launch_rate(gp_ctx *ctx, RateArgs a, int bucket_key_base, const RateTables &t, int64_t nlabels) {
-  const int grid_w = ctx->num_sms * 8;
-  if (MODE == RATE_LP && a.label8 && nlabels <= kDenseLabels) launch_groups<MODE, LK_DENSE>(ctx, a, bucket_key_base);
-  else if (MODE == RATE_LP && a.label8) launch_groups<MODE, LK_NARROW>(ctx, a, bucket_key_base);
-  else launch_groups<MODE, LK_WIDE>(ctx, a, bucket_key_base);
-  a.key = bucket_key_base + 3;
-  k_rate_medium<MODE><<<grid_w, kThreads, 0, ctx->stream>>>(a);
-  GP_LAUNCH_CHECK();
-  a.key = bucket_key_base + 4;
-  a.gkeys = t.gkeys.get();
-  a.gvals = t.gvals.get();
-  a.gstride = t.stride;
-  k_rate_large<MODE><<<t.blocks, kThreads, 0, ctx->stream>>>(a);
-  GP_LAUNCH_CHECK();
+void launch_rate(gp_ctx *ctx, RateArgs a, int bucket_key_base, const RateTables &t, int64_t nlabels,
+                 const int *hcnt) {
+  const int cap = ctx->num_sms * 8;
+  if (MODE == RATE_LP && a.label8 && nlabels <= kDenseLabels) launch_groups<MODE, LK_DENSE>(ctx, a, bucket_key_base, hcnt);
+  else if (MODE == RATE_LP && a.label8) launch_groups<MODE, LK_NARROW>(ctx, a, bucket_key_base, hcnt);
+  else launch_groups<MODE, LK_WIDE>(ctx, a, bucket_key_base, hcnt);
+  if (!hcnt || hcnt[3] > 0) {
+    a.key = bucket_key_base + 3;
+    k_rate_medium<MODE><<<rate_grid(ctx, hcnt ? hcnt[3] : -1, kWarpsPerBlock, cap), kThreads, 0, ctx->stream>>>(a);
+    GP_LAUNCH_CHECK();
+  }
+  if (!hcnt || hcnt[4] > 0) {
+    a.key = bucket_key_base + 4;
+    a.gkeys = t.gkeys.get();
+    a.gvals = t.gvals.get();
+    a.gstride = t.stride;
+    k_rate_large<MODE><<<rate_grid(ctx, hcnt ? hcnt[4] : -1, 1, t.blocks), kThreads, 0, ctx->stream>>>(a);
+    GP_LAUNCH_CHECK();
+  }
 }
 
 }  // namespace
@@ -952,6 +1087,8 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   }
   DBuf<Counters> counters(ctx, 1);
   Counters *C = counters.get();
+  DBuf<unsigned> done(ctx, 1);
+  done.zero();
   k_fill_i32<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(target.get(), n, -1);
   GP_LAUNCH_CHECK();
   incoming.zero();
@@ -965,6 +1102,9 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
 
   TraceTimer trace(ctx);
   const int grid = ctx->num_sms * 8;
+  std::vector<int32_t> hoffs((size_t)nkeys + 1);
+  double sync_s = 0;  // host time blocked in the per-sub-round read of the counters (tracing)
+  const auto t_host0 = std::chrono::steady_clock::now();
   const bool agg = nlabels <= 4096;  // refinement: few labels, aggregate weight updates
   bool stop = n == 0 || (p.count_clusters && ncl0 <= p.n_min);
   int32_t subs = 0;
@@ -984,6 +1124,11 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
                                                                                list.get());
       GP_LAUNCH_CHECK();
     }
+    // bucket sizes of the round (launch shapes, empty buckets skipped) and the stop flag
+    int stop_now = 0;
+    read_back(ctx, &C->stop, sizeof(int), &stop_now);
+    if (stop_now) { stop = true; break; }
+    read_back(ctx, offs.get(), sizeof(int32_t) * (nkeys + 1), hoffs.data());
     for (int s = 0; s < S; s++) {
       if (p.dbg_max_subrounds >= 0 && subs >= p.dbg_max_subrounds) { stop = true; break; }
       RateArgs a{};
@@ -993,20 +1138,23 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       a.stop = &C->stop; a.units = units_rate; a.label8 = label8;
       {
         ProfScope ps(ctx, p.prof_rate);
-        launch_rate<RATE_LP>(ctx, a, s * kNumBuckets, tables, nlabels);
+        int hcnt[kNumBuckets];
+        for (int b = 0; b < kNumBuckets; b++) hcnt[b] = hoffs[s * kNumBuckets + b + 1] - hoffs[s * kNumBuckets + b];
+        launch_rate<RATE_LP>(ctx, a, s * kNumBuckets, tables, nlabels, hcnt);
       }
       const int k0 = s * kNumBuckets, k1 = s * kNumBuckets + kNumBuckets;
+      const int active = hoffs[k1] - hoffs[k0];
       {
         ProfScope ps(ctx, p.prof_accept);
-        k_reset_lists<<<1, 1, 0, ctx->stream>>>(C);
-        GP_LAUNCH_CHECK();
-        k_decide<<<grid, kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(), weight,
+        k_decide<<<grid_for(active, kThreads, grid), kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(), weight,
                                                       incoming.get(), p.bound, mov_v.get(), mov_k.get(),
                                                       ov_key.get(), ov_val.get(), C, kprio);
         GP_LAUNCH_CHECK();
       }
       int hdr[3];
+      const auto t_sync0 = std::chrono::steady_clock::now();
       read_back(ctx, C, sizeof(hdr), hdr);
+      sync_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_sync0).count();
       if (hdr[0]) { stop = true; break; }
       const int nov = hdr[1], nmov = hdr[2];
       subs++;
@@ -1034,6 +1182,11 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
                                                             g.vwgt, weight, ovb_base.get(), p.bound,
                                                             ov_acc.get());
         GP_LAUNCH_CHECK();
+      } else if (nov > 0 && nov <= kOvSmall) {
+        ProfScope ps(ctx, p.prof_overflow);
+        k_ov_small<<<1, kOvSmallThreads, 0, ctx->stream>>>(ov_key.get(), ov_val.get(), nov, g.vwgt, weight,
+                                                           p.bound, ov_acc.get());
+        GP_LAUNCH_CHECK();
       } else if (nov > 0) {
         ProfScope ps(ctx, p.prof_overflow);
         const int kbits = bits_for(nlabels) + 32;
@@ -1060,34 +1213,30 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         if (nmov + nov > 0) {
           k_apply<<<ga, kThreads, sizeof(int) * aa.nshared, ctx->stream>>>(aa);
           GP_LAUNCH_CHECK();
-          k_finalize<<<ga, kThreads, 0, ctx->stream>>>(aa);
-          GP_LAUNCH_CHECK();
         }
-        if (p.count_clusters) {
-          k_count_nonempty<<<grid_for(nlabels / 4 + 1, kThreads, grid), kThreads, 0, ctx->stream>>>(weight, nlabels,
-                                                                                                  C);
-          GP_LAUNCH_CHECK();
-        }
-        k_subround_end<<<1, 1, 0, ctx->stream>>>(C, p.count_clusters ? 1 : 0, (long long)p.n_min);
+        const int64_t count_labels = p.count_clusters ? nlabels : 0;
+        const int gc = grid_for(std::max<int64_t>((int64_t)nmov + nov, count_labels / 4), kThreads, grid);
+        k_close<<<gc, kThreads, 0, ctx->stream>>>(aa, count_labels, (long long)p.n_min, s == S - 1 ? 1 : 0,
+                                                  done.get());
         GP_LAUNCH_CHECK();
       }
     }
     if (stop) break;
-    k_round_end<<<1, 1, 0, ctx->stream>>>(C);
-    GP_LAUNCH_CHECK();
   }
   Counters hc;
   read_back(ctx, C, sizeof(Counters), &hc);
   res.subrounds = subs;
   res.moves = hc.moved_total;
   res.nclusters = hc.nclusters;
-  if (trace.on())
+  if (trace.on()) {
+    const double host_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
     fprintf(stderr,
             "[gp lp] %s level=%d n=%d m2=%lld labels=%lld subrounds=%d moves=%lld proposals=%lld "
-            "overflow_total=%lld overflow_max=%lld ms=%.2f\n",
+            "overflow_total=%lld overflow_max=%lld host_ms=%.2f sync_ms=%.2f ms=%.2f\n",
             p.count_clusters ? "cluster" : "refine", p.level, n, (long long)g.m2, (long long)nlabels, subs,
             (long long)res.moves, (long long)res.proposals, (long long)res.overflow_total,
-            (long long)res.overflow_max, trace.ms());
+            (long long)res.overflow_max, 1000 * host_s, 1000 * sync_s, trace.ms());
+  }
   if (p.count_clusters && nclusters_dev)
     GP_CUDA(cudaMemcpyAsync(nclusters_dev, &C->nclusters, sizeof(int64_t), cudaMemcpyDeviceToDevice,
                             ctx->stream));
@@ -1133,7 +1282,7 @@ void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, c
   a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
   a.label = label; a.weight = nullptr; a.list = list.get(); a.offs = offs.get();
   a.bound = U; a.ktie = kfav; a.fav_keys = keys.get(); a.stop = nullptr;
-  launch_rate<RATE_FAV>(ctx, a, 0, tables, 0);
+  launch_rate<RATE_FAV>(ctx, a, 0, tables, 0, nullptr);
 }
 
 }  // namespace gp

@@ -13,7 +13,8 @@ void *dev_alloc(gp_ctx *ctx, size_t bytes) {
   if (ctx->alloc.alloc) {
     p = ctx->alloc.alloc(bytes, ctx->alloc.user, (void *)ctx->stream);
   } else {
-    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(&p, bytes, ctx->pool, ctx->stream)
+                              : cudaMallocAsync(&p, bytes, ctx->stream);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       p = nullptr;

@@ -354,3 +354,16 @@ def test_validation_errors(gp, ctx):
     # the context stays usable after errors
     blocks, cut, _ = ctx.gp_partition(gp.DeviceGraph.from_host(g), 2, 0.03, 1)
     assert cut == orc.partition(g, 2, 0.03, 1).cut
+
+
+def test_partition_through_torch_allocator(gp):
+    """The same partition when device memory comes from torch's caching allocator."""
+    c = gp.Context(0, use_torch_allocator=True)
+    try:
+        g = GRAPHS["er_w"]
+        dg = gp.DeviceGraph.from_host(g)
+        blocks, cut, _ = c.gp_partition(dg, 8, 0.03, 2)
+        r = orc.partition(g, 8, 0.03, 2)
+        assert cut == r.cut and np.array_equal(blocks.cpu().numpy(), r.blocks)
+    finally:
+        c.close()
