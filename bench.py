@@ -44,7 +44,7 @@ FALLBACK_HBM_GBS = 6800.0
 COARSEN_CLASSES = ("lp_rate", "lp_accept", "lp_overflow", "lp_apply", "two_hop", "relabel", "contract",
                    "contract_aux", "sparsify")
 # ncu DRAM traffic per algorithmic byte, by class, with the sources the counters were taken on
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
 
 def log(*a):
