@@ -53,8 +53,9 @@ typedef struct gp_graph {
 /*
  * Device-memory allocator.  alloc returns `bytes` of device memory usable in
  * stream order on `stream` (NULL on failure); free returns memory allocated
- * by alloc.  When no allocator is given the library uses cudaMallocAsync /
- * cudaFreeAsync on the context stream.
+ * by alloc.  When no allocator is given the library allocates from a private
+ * stream-ordered memory pool of the context (cudaMallocFromPoolAsync on the
+ * context stream) that keeps freed memory for reuse until gp_destroy.
  */
 typedef struct gp_allocator {
   void *(*alloc)(size_t bytes, void *user, void *stream);
