@@ -28,6 +28,7 @@ namespace gp {
 
 namespace {
 
+constexpr int kUpdUnroll = 4;
 constexpr int kChunkNodes = 64;
 constexpr int kMaxSmemBytes = 227 * 1024;
 
@@ -55,7 +56,7 @@ struct IpArgs {
   int32_t *gg;                     // global fallback state per block
   uint8_t *gst;
   uint16_t *gcv;
-  unsigned long long *gbest;
+  unsigned long long *gbest, *gsup;
   int64_t gnodes, gchunks;
   int32_t *gbatch;                 // per block: the nodes taken in the current step
   int batch_cap;
@@ -93,18 +94,22 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
   const Sub S = a.subs[si];
   const int cnt = S.count, nch = (cnt + kChunkNodes - 1) / kChunkNodes;
   const int start = S.start;
-  unsigned long long *best;
+  const int nsup = (nch + 31) / 32;
+  unsigned long long *best, *sup;  // chunk maxima, and maxima over 32 chunks
   int32_t *g;
   uint8_t *st;
   uint16_t *cv = nullptr;
   if (cnt <= a.smem_nodes) {
     const int mch = (a.smem_nodes + kChunkNodes - 1) / kChunkNodes;
+    const int msup = (mch + 31) / 32;
     best = reinterpret_cast<unsigned long long *>(dyn);
-    g = reinterpret_cast<int32_t *>(dyn + sizeof(unsigned long long) * mch);
+    sup = best + mch;
+    g = reinterpret_cast<int32_t *>(dyn + sizeof(unsigned long long) * (mch + msup));
     if (a.cv16) cv = reinterpret_cast<uint16_t *>(g + a.smem_nodes);
     st = reinterpret_cast<uint8_t *>(g + a.smem_nodes) + (a.cv16 ? 2 * a.smem_nodes : 0);
   } else {
     best = a.gbest + (int64_t)blockIdx.x * a.gchunks;
+    sup = a.gsup + (int64_t)blockIdx.x * ((a.gchunks + 31) / 32);
     g = a.gg + (int64_t)blockIdx.x * a.gnodes;
     st = a.gst + (int64_t)blockIdx.x * a.gnodes;
     if (a.cv16) cv = a.gcv + (int64_t)blockIdx.x * a.gnodes;
@@ -115,6 +120,7 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
     if (cv) cv[j] = (uint16_t)a.cvl[start + j];
   }
   for (int c = lane; c < nch; c += 32) best[c] = 0;
+  for (int c = lane; c < nsup; c += 32) sup[c] = 0;
   __syncwarp();
   const uint64_t kip = stream_key(a.seed, TAG_IP, 0, (uint32_t)S.bid);
   int64_t w1 = 0;
@@ -125,7 +131,7 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
     int nb = 0;
     while (nb < B && w1 < S.T1) {
       unsigned long long b = 0;
-      for (int c = lane; c < nch; c += 32) b = best[c] > b ? best[c] : b;
+      for (int c = lane; c < nsup; c += 32) b = sup[c] > b ? sup[c] : b;
       b = warp_max(b);
       if (b == 0) break;
       const int j = (int)(0xFFFFFFFFu - (unsigned)(b & 0xFFFFFFFFull));
@@ -138,7 +144,13 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
       }
       if (fit) { nb++; w1 += cj; }
       __syncwarp();
-      rescan_chunk(j / kChunkNodes, cnt, g, st, best);
+      const int c = j / kChunkNodes;
+      rescan_chunk(c, cnt, g, st, best);
+      const int s0 = (c / 32) * 32;  // the maximum over c's 32 chunks again
+      unsigned long long x = s0 + lane < nch ? best[s0 + lane] : 0;
+      x = warp_max(x);
+      if (lane == 0) sup[c / 32] = x;
+      __syncwarp();
     }
     if (a.trace && lane == 0) atomicAdd(a.trace + 0, 1ull);
     if (nb == 0) {  // no frontier node fits: the smallest-hash node that fits
@@ -176,22 +188,33 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
         if (lane >= o) incl += y;
       }
       const int excl = incl - d, total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      for (int f0 = 0; f0 < total; f0 += 32) {
-        const int f = f0 + lane;
-        int q = 0;
+      for (int f0 = 0; f0 < total; f0 += 32 * kUpdUnroll) {  // four entries per lane in flight
+        int idx[kUpdUnroll];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int val = __shfl_sync(0xFFFFFFFFu, incl, q + step - 1);
-          if (val <= f) q += step;
+        for (int r = 0; r < kUpdUnroll; r++) {
+          const int f = f0 + r * 32 + lane;
+          int q = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int val = __shfl_sync(0xFFFFFFFFu, incl, q + step - 1);
+            if (val <= f) q += step;
+          }
+          const int sq = __shfl_sync(0xFFFFFFFFu, rs, q), eq = __shfl_sync(0xFFFFFFFFu, excl, q);
+          idx[r] = f < total ? sq + (f - eq) : -1;
         }
-        const int sq = __shfl_sync(0xFFFFFFFFu, rs, q), eq = __shfl_sync(0xFFFFFFFFu, excl, q);
-        if (f < total) {
-          const int2 e = a.ladj[sq + (f - eq)];
-          const uint8_t su = st[e.x];
+        int2 e[kUpdUnroll];
+#pragma unroll
+        for (int r = 0; r < kUpdUnroll; r++) e[r] = idx[r] >= 0 ? a.ladj[idx[r]] : make_int2(-1, 0);
+#pragma unroll
+        for (int r = 0; r < kUpdUnroll; r++) {
+          if (e[r].x < 0) continue;
+          const uint8_t su = st[e[r].x];
           if (su == S_FREE || su == S_FRONT) {
-            const int ng = atomicAdd(&g[e.x], 2 * e.y) + 2 * e.y;
-            if (su == S_FREE) st[e.x] = S_FRONT;
-            atomicMax(&best[e.x / kChunkNodes], gain_key(ng, e.x));
+            const int ng = atomicAdd(&g[e[r].x], 2 * e[r].y) + 2 * e[r].y;
+            if (su == S_FREE) st[e[r].x] = S_FRONT;
+            const unsigned long long key = gain_key(ng, e[r].x);
+            atomicMax(&best[e[r].x / kChunkNodes], key);
+            atomicMax(&sup[e[r].x / (32 * kChunkNodes)], key);
           }
         }
       }
@@ -413,14 +436,14 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
     // shared-memory state: chunk maxima (8 B per 64 nodes) + gain (4 B) + weight (2 B, when it fits) +
     // state (1 B) per node
     const int per_node = a.cv16 ? 7 : 5;
-    const int smem_cap = (kMaxSmemBytes - 64) * kChunkNodes / (8 + per_node * kChunkNodes);
+    const int smem_cap = (kMaxSmemBytes - 128) * kChunkNodes / (9 + per_node * kChunkNodes);
     a.smem_nodes = std::max(1, std::min(maxcnt, smem_cap));
-    const size_t smem_bytes = (size_t)((a.smem_nodes + kChunkNodes - 1) / kChunkNodes) * 8 +
-                              (size_t)a.smem_nodes * per_node;
+    const int mch = (a.smem_nodes + kChunkNodes - 1) / kChunkNodes;
+    const size_t smem_bytes = (size_t)(mch + (mch + 31) / 32) * 8 + (size_t)a.smem_nodes * per_node;
     DBuf<int32_t> gg;
     DBuf<uint8_t> gst;
     DBuf<uint16_t> gcv;
-    DBuf<unsigned long long> gbest;
+    DBuf<unsigned long long> gbest, gsup;
     if (maxcnt > a.smem_nodes) {
       a.gnodes = maxcnt;
       a.gchunks = (maxcnt + kChunkNodes - 1) / kChunkNodes;
@@ -428,7 +451,8 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
       gst.reset(ctx, (size_t)nblocks * a.gnodes);
       if (a.cv16) gcv.reset(ctx, (size_t)nblocks * a.gnodes);
       gbest.reset(ctx, (size_t)nblocks * a.gchunks);
-      a.gg = gg.get(); a.gst = gst.get(); a.gcv = gcv.get(); a.gbest = gbest.get();
+      gsup.reset(ctx, (size_t)nblocks * ((a.gchunks + 31) / 32));
+      a.gg = gg.get(); a.gst = gst.get(); a.gcv = gcv.get(); a.gbest = gbest.get(); a.gsup = gsup.get();
     }
     a.trial_cut = tcut.get();
     a.flags = flags.get();

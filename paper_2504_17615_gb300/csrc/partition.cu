@@ -42,7 +42,7 @@ __global__ void k_validate_nodes(const int32_t *xadj, const int32_t *vwgt, int n
 }
 
 __device__ __forceinline__ unsigned long long pair_hash(uint32_t lo, uint32_t hi, int w) {
-  return fmix((((uint64_t)lo << 32) | hi) ^ fmix((uint64_t)(uint32_t)w + kGold));
+  return fmix(((((uint64_t)lo << 32) | hi) + (uint64_t)(uint32_t)w * kGold) ^ kGold);
 }
 
 // Entry checks: ids in range, no self-loop, positive weights, strictly
