@@ -100,12 +100,12 @@ __global__ void __launch_bounds__(kThreads) k_map(const int32_t *xadj, const int
         Aj[r] = __shfl_sync(FULL, A, j);
       }
 #pragma unroll
-      for (int r = 0; r < kMapUnroll; r++) nb[r] = e[r] < e1 ? adjncy[e[r]] : 0;
+      for (int r = 0; r < kMapUnroll; r++) nb[r] = e[r] < e1 ? __ldcs(adjncy + e[r]) : 0;  // read once: evict first
 #pragma unroll
       for (int r = 0; r < kMapUnroll; r++) nb[r] = e[r] < e1 ? cmap[nb[r]] : 0;
 #pragma unroll
       for (int r = 0; r < kMapUnroll; r++)
-        if (e[r] < e1) temp[bj[r] + e[r]] = nb[r] == Aj[r] ? make_int2(-1, 0) : make_int2(nb[r], adjwgt[e[r]]);
+        if (e[r] < e1) temp[bj[r] + e[r]] = nb[r] == Aj[r] ? make_int2(-1, 0) : make_int2(nb[r], __ldcs(adjwgt + e[r]));
     }
   }
   ue = warp_sum(ue);
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(kThreads) k_merge_warp(MergeArgs a) {
     const int bits = table_bits(len), tsize = 1 << bits;
     for (int i0 = s0; i0 < s1; i0 += 64) {  // two entries per lane in flight
       const int i1 = i0 + lane, i2 = i0 + 32 + lane;
-      const int2 x1 = i1 < s1 ? a.temp[i1] : make_int2(-1, 0);
-      const int2 x2 = i2 < s1 ? a.temp[i2] : make_int2(-1, 0);
+      const int2 x1 = i1 < s1 ? __ldcs(a.temp + i1) : make_int2(-1, 0);
+      const int2 x2 = i2 < s1 ? __ldcs(a.temp + i2) : make_int2(-1, 0);
       if (x1.x >= 0) table_add(tk, tv, tsize - 1, bits, x1.x, x1.y);
       if (x2.x >= 0) table_add(tk, tv, tsize - 1, bits, x2.x, x2.y);
     }

@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
 #pragma unroll
     for (int q = 0; q < U; q++) {
       const bool ok = gl < deg[q];
-      u[q] = ok ? a.adjncy[st[q] + gl] : -1;
-      w[q] = ok ? a.adjwgt[st[q] + gl] : 0;
+      u[q] = ok ? __ldcs(a.adjncy + st[q] + gl) : -1;  // rows are read once a round: evict first
+      w[q] = ok ? __ldcs(a.adjwgt + st[q] + gl) : 0;
     }
 #pragma unroll
     for (int q = 0; q < U; q++)
@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
     const int own = label_of(a, v);
     const int cv = a.vwgt[v];
     for (int j = lane; j < deg; j += 32) {
-      const int L = label_of(a, a.adjncy[start + j]);
-      const int w = a.adjwgt[start + j];
+      const int L = label_of(a, __ldcs(a.adjncy + start + j));
+      const int w = __ldcs(a.adjwgt + start + j);
       unsigned s = slot_hash(L, 8);
       for (int probe = 0; probe < kMedSlots; probe++) {  // bounded: the table never fills
         const int prev = atomicCAS(&tk[s], -1, L);
@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
     int *tk = in_smem ? s_k : gk;
     int *tv = in_smem ? s_v : gv;
     for (int j = threadIdx.x; j < deg; j += blockDim.x) {
-      const int L = label_of(a, a.adjncy[start + j]);
-      const int w = a.adjwgt[start + j];
+      const int L = label_of(a, __ldcs(a.adjncy + start + j));
+      const int w = __ldcs(a.adjwgt + start + j);
       unsigned s = slot_hash(L, bits);
       for (int probe = 0; probe < tsize; probe++) {  // bounded: the table never fills
         const int prev = atomicCAS(&tk[s], -1, L);

@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(256) k_keep(KeepArgs a) {
       }
 #pragma unroll
       for (int r = 0; r < kKeepUnroll; r++) {
-        v[r] = e[r] < e1 ? a.adjncy[e[r]] : 0;
-        x[r] = e[r] < e1 ? a.adjwgt[e[r]] : 0;
+        v[r] = e[r] < e1 ? __ldcs(a.adjncy + e[r]) : 0;
+        x[r] = e[r] < e1 ? __ldcs(a.adjwgt + e[r]) : 0;
       }
 #pragma unroll
       for (int r = 0; r < kKeepUnroll; r++) {
