@@ -32,7 +32,7 @@ constexpr int kMaxKeys = 64 * kNumBuckets;
 struct RateArgs {
   const int32_t *xadj, *adjncy, *adjwgt, *vwgt, *label, *weight;
   const uint8_t *label8;  // optional narrow copy of label (fewer than 256 labels) for gathers
-  const int32_t *list;
+  const int4 *list;     // bucket list: (node, row offset, degree, node weight)
   const int32_t *offs;
   int key;
   int64_t bound;
@@ -125,16 +125,13 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
 #pragma unroll
     for (int q = 0; q < U; q++) {
       const int i = base + q * NV + grp;
-      v[q] = i < end ? a.list[i] : -1;
+      const int4 rec = i < end ? a.list[i] : make_int4(-1, 0, 0, 0);
+      v[q] = rec.x; st[q] = rec.y; deg[q] = rec.z; cv[q] = rec.w;
     }
 #pragma unroll
     for (int q = 0; q < U; q++) {
       const bool ok = v[q] >= 0;
-      const int vv = ok ? v[q] : 0;
-      st[q] = a.xadj[vv];
-      deg[q] = ok ? a.xadj[vv + 1] - st[q] : 0;
-      own[q] = ok ? (LK == LK_WIDE ? a.label[vv] : (int)a.label8[vv]) : -2;
-      cv[q] = a.vwgt[vv];
+      own[q] = ok ? (LK == LK_WIDE ? a.label[v[q]] : (int)a.label8[v[q]]) : -2;
     }
 #pragma unroll
     for (int q = 0; q < U; q++) {
@@ -285,11 +282,9 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
   for (int i = begin + wid; i < end; i += nw) {
-    const int v = a.list[i];
-    const int start = a.xadj[v];
-    const int deg = a.xadj[v + 1] - start;
+    const int4 rec = a.list[i];
+    const int v = rec.x, start = rec.y, deg = rec.z, cv = rec.w;
     const int own = label_of(a, v);
-    const int cv = a.vwgt[v];
     for (int j = lane; j < deg; j += 32) {
       const int L = label_of(a, __ldcs(a.adjncy + start + j));
       const int w = __ldcs(a.adjwgt + start + j);
@@ -370,11 +365,9 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
   int *gv = a.gvals ? a.gvals + (int64_t)blockIdx.x * a.gstride : nullptr;
   unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
   for (int i = begin + (int)blockIdx.x; i < end; i += (int)gridDim.x) {
-    const int v = a.list[i];
-    const int start = a.xadj[v];
-    const int deg = a.xadj[v + 1] - start;
+    const int4 rec = a.list[i];
+    const int v = rec.x, start = rec.y, deg = rec.z, cv = rec.w;
     const int own = label_of(a, v);
-    const int cv = a.vwgt[v];
     int bits = 1;
     while ((1 << bits) < 2 * deg) bits++;
     const int tsize = 1 << bits;
@@ -479,7 +472,7 @@ __global__ void k_bucket_offsets(const int *cnt, int nkeys, int *offs, int *curs
 }
 
 __global__ void __launch_bounds__(kThreads) k_bucket_scatter(BucketArgs b, int nkeys, int *cursor,
-                                                             int32_t *list) {
+                                                             int4 *list) {
   __shared__ int s_c[kMaxKeys];
   __shared__ int s_base[kMaxKeys];
   if (b.stop && *b.stop) return;
@@ -504,7 +497,8 @@ __global__ void __launch_bounds__(kThreads) k_bucket_scatter(BucketArgs b, int n
       if (keys[j] < 0) continue;
       const int64_t v = c0 + j * kThreads + threadIdx.x;
       const int pos = s_base[keys[j]] + atomicAdd(&s_c[keys[j]], 1);
-      list[pos] = (int32_t)v;
+      const int st = b.xadj[v];
+      list[pos] = make_int4((int)v, st, b.xadj[v + 1] - st, b.vwgt[v]);
     }
     __syncthreads();
   }
@@ -529,7 +523,7 @@ struct Counters {
 // target's snapshot weight plus all incoming weight fits) or to the list of
 // proposers of overflowing targets.  Slots in both lists are reserved once
 // per block and iteration.
-__global__ void __launch_bounds__(kThreads) k_decide(const int32_t *list, const int32_t *offs,
+__global__ void __launch_bounds__(kThreads) k_decide(const int4 *list, const int32_t *offs,
                                                      int k0, int k1, int32_t *target,
                                                      const int32_t *weight, const int32_t *incoming,
                                                      int64_t bound, int32_t *mov_v, int32_t *mov_k,
@@ -545,7 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const int32_t *list, const 
     bool acc = false, over = false;
     int v = 0, K = -1;
     if (i < end) {
-      v = list[i];
+      v = list[i].x;
       K = target[v];
       if (K >= 0) {
         target[v] = -1;
@@ -1062,7 +1056,8 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   const int S = p.subrounds;
   GP_REQUIRE(S >= 1 && S <= 64, GP_ERR_INVALID, "lp_subrounds must be in [1, 64]");
   const int nkeys = S * kNumBuckets;
-  DBuf<int32_t> list(ctx, (size_t)n), target(ctx, (size_t)n), incoming(ctx, (size_t)nlabels);
+  DBuf<int4> list(ctx, (size_t)n);
+  DBuf<int32_t> target(ctx, (size_t)n), incoming(ctx, (size_t)nlabels);
   DBuf<int32_t> cnt(ctx, (size_t)nkeys), offs(ctx, (size_t)nkeys + 1), cursor(ctx, (size_t)nkeys);
   DBuf<int32_t> mov_v(ctx, (size_t)n), mov_k(ctx, (size_t)n);
   DBuf<uint64_t> ov_key(ctx, (size_t)n);
@@ -1258,7 +1253,8 @@ void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, c
   const int n = g.n;
   const int nkeys = kNumBuckets;
   const int grid = ctx->num_sms * 8;
-  DBuf<int32_t> list(ctx, (size_t)n), cnt(ctx, (size_t)nkeys), offs(ctx, (size_t)nkeys + 1),
+  DBuf<int4> list(ctx, (size_t)n);
+  DBuf<int32_t> cnt(ctx, (size_t)nkeys), offs(ctx, (size_t)nkeys + 1),
       cursor(ctx, (size_t)nkeys);
   BucketArgs b{g.xadj, label, size, g.vwgt, n, 0, 1, 1, U, nullptr};
   cnt.zero();
