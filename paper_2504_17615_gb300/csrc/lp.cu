@@ -37,7 +37,7 @@ struct RateArgs {
   int key;
   int64_t bound;
   uint64_t ktie;
-  int32_t *target;      // RATE_LP: per node proposal (-1 none)
+  int2 *prop;           // RATE_LP: per list position (proposed label or -1, own label)
   int32_t *incoming;    // RATE_LP: per label incoming weight
   uint64_t *fav_keys;   // RATE_FAV: per list position (fav << 32 | v)
   const int *stop;
@@ -69,9 +69,9 @@ __device__ __forceinline__ unsigned slot_hash(int L, int bits) {
 }
 
 template <int MODE>
-__device__ __forceinline__ void emit(const RateArgs &a, int i, int v, int best, int cv) {
+__device__ __forceinline__ void emit(const RateArgs &a, int i, int v, int best, int cv, int own) {
   if (MODE == RATE_LP) {
-    a.target[v] = best;
+    a.prop[i] = make_int2(best, own);
     atomicAdd(&a.incoming[best], cv);
   } else {
     a.fav_keys[i] = ((uint64_t)(uint32_t)best << 32) | (uint32_t)v;
@@ -99,7 +99,7 @@ enum LabelKind { LK_WIDE = 0, LK_NARROW = 1, LK_DENSE = 2 };
 constexpr int kDenseLabels = 128;
 
 template <int MODE, int G, int U, int LK>
-__global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
+__global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateArgs a) {
   static_assert(G == 8 || G == 16 || G == 32, "group width");
   constexpr int NV = 32 / G;
   constexpr int PER = NV * U;
@@ -257,8 +257,10 @@ __global__ void __launch_bounds__(kThreads) k_rate_group(RateArgs a) {
         ue += deg[q];
         uv += 1;
         if (best[q] != 0xFFFFFFFFu) {
-          emit<MODE>(a, base + q * NV + grp, v[q], (int)best[q], cv[q]);
+          emit<MODE>(a, base + q * NV + grp, v[q], (int)best[q], cv[q], own[q]);
           up += 1;
+        } else if (MODE == RATE_LP) {
+          a.prop[base + q * NV + grp] = make_int2(-1, 0);
         }
       }
     }
@@ -319,7 +321,9 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
         packed = p < packed ? p : packed;
       }
       packed = warp_min(packed);
-      if (lane == 0) { emit<MODE>(a, i, v, (int)(uint32_t)packed, cv); up += 1; }
+      if (lane == 0) { emit<MODE>(a, i, v, (int)(uint32_t)packed, cv, own); up += 1; }
+    } else if (MODE == RATE_LP && lane == 0) {
+      a.prop[i] = make_int2(-1, 0);
     }
     for (int t = lane; t < kMedSlots; t += 32) { tk[t] = -1; tv[t] = 0; }
     __syncwarp();
@@ -409,7 +413,9 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
         packed = p < packed ? p : packed;
       }
       packed = block_min_u64(packed, s_ru);
-      if (threadIdx.x == 0) { emit<MODE>(a, i, v, (int)(uint32_t)packed, cv); up += 1; }
+      if (threadIdx.x == 0) { emit<MODE>(a, i, v, (int)(uint32_t)packed, cv, own); up += 1; }
+    } else if (MODE == RATE_LP && threadIdx.x == 0) {
+      a.prop[i] = make_int2(-1, 0);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < tsize; t += blockDim.x) { tk[t] = -1; tv[t] = 0; }
@@ -518,15 +524,15 @@ struct Counters {
   long long nclusters;
 };
 
-// Every active node's proposal is read once: the node's slot in `target` is
-// reset, and the proposal goes to the list of outright acceptances (the
-// target's snapshot weight plus all incoming weight fits) or to the list of
-// proposers of overflowing targets.  Slots in both lists are reserved once
-// per block and iteration.
+// Every active node's proposal (written by the rating kernels at its list
+// position) goes to the list of outright acceptances (the target's snapshot
+// weight plus all incoming weight fits), as a (node, target, own label,
+// weight) record, or to the list of proposers of overflowing targets.  Slots
+// in both lists are reserved once per block and iteration.
 __global__ void __launch_bounds__(kThreads) k_decide(const int4 *list, const int32_t *offs,
-                                                     int k0, int k1, int32_t *target,
+                                                     int k0, int k1, const int2 *prop,
                                                      const int32_t *weight, const int32_t *incoming,
-                                                     int64_t bound, int32_t *mov_v, int32_t *mov_k,
+                                                     int64_t bound, int4 *mov,
                                                      uint64_t *ov_key, uint32_t *ov_val, Counters *cnt,
                                                      uint64_t kprio) {
   __shared__ int s_a[kWarpsPerBlock + 1], s_o[kWarpsPerBlock + 1];
@@ -537,12 +543,13 @@ __global__ void __launch_bounds__(kThreads) k_decide(const int4 *list, const int
   for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += stride) {
     const int i = base + (int)threadIdx.x;
     bool acc = false, over = false;
-    int v = 0, K = -1;
+    int v = 0, K = -1, own = 0, c = 0;
     if (i < end) {
-      v = list[i].x;
-      K = target[v];
+      const int2 pr = prop[i];
+      K = pr.x;
       if (K >= 0) {
-        target[v] = -1;
+        const int4 rec = list[i];
+        v = rec.x; c = rec.w; own = pr.y;
         if ((int64_t)weight[K] + incoming[K] <= bound) acc = true;
         else over = true;
       }
@@ -563,8 +570,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const int4 *list, const int
     __syncthreads();
     if (acc) {
       const int pos = s_a[kWarpsPerBlock] + s_a[w] + __popc(ma & lanemask_lt());
-      mov_v[pos] = v;
-      mov_k[pos] = K;
+      mov[pos] = make_int4(v, K, own, c);
     }
     if (over) {
       const int pos = s_o[kWarpsPerBlock] + s_o[w] + __popc(mo & lanemask_lt());
@@ -820,7 +826,7 @@ __global__ void __launch_bounds__(256) k_ovb_resolve(const uint64_t *bkey, const
 }
 
 struct ApplyArgs {
-  const int32_t *mov_v, *mov_k;
+  const int4 *mov;  // outright moves: (node, target, own label, node weight)
   const uint64_t *ov_key;
   const uint32_t *ov_val;
   const uint8_t *ov_acc;
@@ -832,12 +838,16 @@ struct ApplyArgs {
   Counters *cnt;
 };
 
-__device__ __forceinline__ void proposal(const ApplyArgs &a, int t, int &v, int &K, bool &mv) {
+__device__ __forceinline__ void proposal(const ApplyArgs &a, int t, int &v, int &K, int &own, int &c,
+                                         bool &mv) {
   if (t < a.nmov) {
-    v = a.mov_v[t]; K = a.mov_k[t]; mv = true;
+    const int4 r = a.mov[t];
+    v = r.x; K = r.y; own = r.z; c = r.w; mv = true;
   } else {
     const int j = t - a.nmov;
     v = (int)a.ov_val[j]; K = (int)(a.ov_key[j] >> 32); mv = a.ov_acc[j] != 0;
+    own = mv ? a.label[v] : 0;
+    c = mv ? a.vwgt[v] : 0;
   }
 }
 
@@ -849,11 +859,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
   const int total = a.nmov + a.nov;
   long long moved = 0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    int v, K;
+    int v, K, own, c;
     bool mv;
-    proposal(a, t, v, K, mv);
+    proposal(a, t, v, K, own, c, mv);
     if (mv) {
-      const int own = a.label[v], c = a.vwgt[v];
       a.label[v] = K;
       if (a.label8) a.label8[v] = (uint8_t)K;
       if (a.nshared) {
@@ -888,7 +897,7 @@ __global__ void __launch_bounds__(kThreads) k_close(ApplyArgs a, int64_t count_l
   if (cnt->stop) return;
   const int total = a.nmov + a.nov;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int K = t < a.nmov ? a.mov_k[t] : (int)(a.ov_key[t - a.nmov] >> 32);
+    const int K = t < a.nmov ? a.mov[t].y : (int)(a.ov_key[t - a.nmov] >> 32);
     a.incoming[K] = 0;
   }
   if (count_labels > 0) {
@@ -1057,9 +1066,10 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   GP_REQUIRE(S >= 1 && S <= 64, GP_ERR_INVALID, "lp_subrounds must be in [1, 64]");
   const int nkeys = S * kNumBuckets;
   DBuf<int4> list(ctx, (size_t)n);
-  DBuf<int32_t> target(ctx, (size_t)n), incoming(ctx, (size_t)nlabels);
+  DBuf<int2> prop(ctx, (size_t)n);
+  DBuf<int32_t> incoming(ctx, (size_t)nlabels);
   DBuf<int32_t> cnt(ctx, (size_t)nkeys), offs(ctx, (size_t)nkeys + 1), cursor(ctx, (size_t)nkeys);
-  DBuf<int32_t> mov_v(ctx, (size_t)n), mov_k(ctx, (size_t)n);
+  DBuf<int4> mov(ctx, (size_t)n);
   DBuf<uint64_t> ov_key(ctx, (size_t)n);
   DBuf<uint32_t> ov_val(ctx, (size_t)n);
   DBuf<uint8_t> ov_acc(ctx, (size_t)n);
@@ -1084,8 +1094,6 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   Counters *C = counters.get();
   DBuf<unsigned> done(ctx, 1);
   done.zero();
-  k_fill_i32<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(target.get(), n, -1);
-  GP_LAUNCH_CHECK();
   incoming.zero();
   int64_t ncl0 = 0;
   if (p.count_clusters && nclusters_dev) read_back(ctx, nclusters_dev, sizeof(int64_t), &ncl0);
@@ -1129,7 +1137,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       RateArgs a{};
       a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
       a.label = label; a.weight = weight; a.list = list.get(); a.offs = offs.get();
-      a.bound = p.bound; a.ktie = ktie; a.target = target.get(); a.incoming = incoming.get();
+      a.bound = p.bound; a.ktie = ktie; a.prop = prop.get(); a.incoming = incoming.get();
       a.stop = &C->stop; a.units = units_rate; a.label8 = label8;
       {
         ProfScope ps(ctx, p.prof_rate);
@@ -1141,8 +1149,8 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       const int active = hoffs[k1] - hoffs[k0];
       {
         ProfScope ps(ctx, p.prof_accept);
-        k_decide<<<grid_for(active, kThreads, grid), kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, target.get(), weight,
-                                                      incoming.get(), p.bound, mov_v.get(), mov_k.get(),
+        k_decide<<<grid_for(active, kThreads, grid), kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, prop.get(), weight,
+                                                      incoming.get(), p.bound, mov.get(),
                                                       ov_key.get(), ov_val.get(), C, kprio);
         GP_LAUNCH_CHECK();
       }
@@ -1200,7 +1208,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       {
         ProfScope ps(ctx, p.prof_apply);
         ApplyArgs aa{};
-        aa.mov_v = mov_v.get(); aa.mov_k = mov_k.get(); aa.ov_key = ov_key.get(); aa.ov_val = ov_val.get();
+        aa.mov = mov.get(); aa.ov_key = ov_key.get(); aa.ov_val = ov_val.get();
         aa.ov_acc = ov_acc.get(); aa.nmov = nmov; aa.nov = nov; aa.vwgt = g.vwgt; aa.label = label;
         aa.weight = weight; aa.incoming = incoming.get(); aa.label8 = label8;
         aa.nshared = agg ? (int)nlabels : 0; aa.cnt = C;
