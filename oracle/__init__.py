@@ -102,6 +102,8 @@ def _load():
             sig = {
                 "or_key": (u64, [u64, u32, u32, u32]),
                 "or_h32": (u32, [u64, u32, u32]),
+                "or_h64": (u64, [u64, u32, u32]),
+                "or_modularity": (ctypes.c_int, [i32, P, P, P, P, i32, P]),
                 "or_validate": (ctypes.c_int, G + [P]),
                 "or_lmax": (i64, [i64, i32, i64]),
                 "or_cluster_bound": (i64, [i64, i32, i32]),
@@ -243,6 +245,46 @@ def sparsify(g, m_hat: int, level: int, seed: int, mode: int = 1):
     if rc != OK:
         raise RuntimeError(f"or_sparsify failed: {rc}")
     return _take_graph(g.n, *[p.value for p in ptrs]), st
+
+
+def h64(k: int, x: int, y: int) -> int:
+    """All 64 bits of the mix behind h32 (the order of the exact-count sampler)."""
+    return _load().or_h64(k, x, y)
+
+
+@dataclass
+class Modularity:
+    """Sec. 5 for a clustering, from exact integer totals over the CSR entries."""
+    w_internal: int
+    w_total: int
+    vol_max: int
+    vol_sq: int
+
+    @property
+    def inside(self) -> float:  # sum_i e_ii
+        return self.w_internal / self.w_total
+
+    @property
+    def q(self) -> float:  # Q_C
+        return self.inside - self.vol_sq / float(self.w_total) ** 2
+
+    @property
+    def alpha(self) -> float:  # alpha_C
+        return self.vol_max / self.w_total
+
+    @property
+    def bound(self) -> float:  # Lemma 2: lower bound of the weight fraction between clusters
+        return 1.0 - self.q - self.alpha
+
+
+def modularity(g, labels, nlabels: int) -> Modularity:
+    keep, a = _args(g)
+    lab, plab = _c(labels, np.int32)
+    out = np.zeros(4, dtype=np.int64)
+    rc = _load().or_modularity(g.n, a[1], a[2], a[4], plab, nlabels, out.ctypes.data)
+    if rc != OK:
+        raise RuntimeError(f"or_modularity failed: {rc}")
+    return Modularity(int(out[0]), int(out[1]), int(out[2]), int(np.uint64(out[3])))
 
 
 def m_hat(m: int, n: int, n_next: int, cfg: Config | None = None) -> int:

@@ -44,6 +44,11 @@ uint32_t or_h32(uint64_t key, uint32_t x, uint32_t y) {
   return (uint32_t)(mix(key ^ (((uint64_t)x << 32) | (uint64_t)y)) >> 32);
 }
 
+/* all 64 bits of the same mix: the order of the exact-count sampler */
+uint64_t or_h64(uint64_t key, uint32_t x, uint32_t y) {
+  return mix(key ^ (((uint64_t)x << 32) | (uint64_t)y));
+}
+
 /* ----------------------------------------------------------------- graph */
 
 typedef struct {
@@ -492,6 +497,27 @@ static int cmp_desc_i32(const void *a, const void *b) {
  * Uniform sampling (mode 2): keep iff h32(key(UNIFORM, level, 0), min, max)
  * < floor(m_hat * 2^32 / m).  Weights are kept unchanged (R17).
  */
+typedef struct {
+  uint64_t h;
+  uint32_t lo, hi;
+} heq_t;
+
+static int heq_cmp(const void *a, const void *b) {
+  const heq_t *x = (const heq_t *)a, *y = (const heq_t *)b;
+  if (x->h != y->h) return x->h < y->h ? -1 : 1;
+  if (x->lo != y->lo) return x->lo < y->lo ? -1 : 1;
+  if (x->hi != y->hi) return x->hi < y->hi ? -1 : 1;
+  return 0;
+}
+
+/*
+ * Sec. 4.2 sampling of the edges of weight omega_t.  Modes: 1 T-Weight (each
+ * such edge kept with probability (m_hat - |E>|) / |E=| by a hash draw), 2 UR
+ * (every edge with probability m_hat / m), 3 exact-count T-Weight: of the edges
+ * of weight omega_t exactly m_hat - |E>| are kept, those first in the order of
+ * (64-bit hash of the endpoints, min, max), so the level keeps exactly m_hat
+ * edges.
+ */
 static int sparsify(const og *g, int64_t m_hat, int32_t level, uint64_t seed, int mode, og *out,
                     or_sparse_stats *st) {
   int32_t n = g->n;
@@ -517,6 +543,26 @@ static int sparsify(const og *g, int64_t m_hat, int32_t level, uint64_t seed, in
       free(ws);
     }
   }
+  heq_t bound = {0, 0, 0};  /* mode 3: the last kept edge of weight omega_t in the hash order */
+  if (mode == 3 && !keep_all && !keep_none) {
+    heq_t *eq = (heq_t *)malloc(sizeof(heq_t) * ((size_t)ne + 1));
+    if (!eq) return OR_NOMEM;
+    int64_t c = 0;
+    for (int32_t u = 0; u < n; u++)
+      for (int64_t j = g->xadj[u]; j < g->xadj[u + 1]; j++) {
+        int32_t v = g->adjncy[j];
+        if (u < v && g->adjwgt[j] == wt) {
+          eq[c].h = or_h64(key, (uint32_t)u, (uint32_t)v);
+          eq[c].lo = (uint32_t)u;
+          eq[c].hi = (uint32_t)v;
+          c++;
+        }
+      }
+    qsort(eq, (size_t)c, sizeof(heq_t), heq_cmp);
+    bound = eq[m_hat - ng - 1];
+    T = bound.h;
+    free(eq);
+  }
   if (og_alloc(out, n, g->m2)) return OR_NOMEM;
   int64_t w = 0;
   for (int32_t u = 0; u < n; u++) {
@@ -531,7 +577,10 @@ static int sparsify(const og *g, int64_t m_hat, int32_t level, uint64_t seed, in
         uint32_t lo = (uint32_t)(u < v ? u : v), hi = (uint32_t)(u < v ? v : u);
         uint64_t h = or_h32(key, lo, hi);
         if (mode == 2) keep = h < T;
-        else keep = ew > wt || (ew == wt && h < T);
+        else if (mode == 3) {
+          heq_t x = {or_h64(key, lo, hi), lo, hi};
+          keep = ew > wt || (ew == wt && heq_cmp(&x, &bound) <= 0);
+        } else keep = ew > wt || (ew == wt && h < T);
       }
       if (keep) { out->adjncy[w] = v; out->adjwgt[w] = ew; w++; }
     }
@@ -800,6 +849,45 @@ int or_contract(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int
   int rc = contract(&g, cmap, nc, &out);
   *oxadj = out.xadj; *oadjncy = out.adjncy; *ovwgt = out.vwgt; *oadjwgt = out.adjwgt;
   return rc;
+}
+
+/*
+ * Modularity of a clustering (Sec. 5): with e_ij the fraction of the edge
+ * weight running from cluster i to cluster j (each direction counted, so the
+ * fractions sum to one), a_i = sum_j e_ij, Q_C = sum_i (e_ii - a_i^2) and
+ * alpha_C = max_i a_i; Lemma 2 bounds the weight fraction inside clusters by
+ * Q_C <= sum_i e_ii <= Q_C + alpha_C, so 1 - Q_C - alpha_C bounds the fraction
+ * between clusters from below.  Returned as exact integers over the CSR
+ * entries: out[0] weight inside clusters, out[1] total weight (both
+ * directions), out[2] largest cluster volume, out[3] sum of squared volumes
+ * (unsigned).  label[v] must lie in [0, nlabels).
+ */
+int or_modularity(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                  const int32_t *label, int32_t nlabels, int64_t *out) {
+  uint64_t *vol = (uint64_t *)calloc((size_t)nlabels + 1, sizeof(uint64_t));
+  if (!vol) return OR_NOMEM;
+  int64_t win = 0, wtot = 0;
+  for (int32_t u = 0; u < n; u++) {
+    if (label[u] < 0 || label[u] >= nlabels) { free(vol); return OR_INVALID; }
+    for (int64_t j = xadj[u]; j < xadj[u + 1]; j++) {
+      int32_t v = adjncy[j];
+      if (label[v] < 0 || label[v] >= nlabels) { free(vol); return OR_INVALID; }
+      wtot += adjwgt[j];
+      vol[label[u]] += (uint64_t)adjwgt[j];
+      if (label[u] == label[v]) win += adjwgt[j];
+    }
+  }
+  uint64_t vmax = 0, sq = 0;
+  for (int32_t i = 0; i < nlabels; i++) {
+    if (vol[i] > vmax) vmax = vol[i];
+    sq += vol[i] * vol[i];
+  }
+  free(vol);
+  out[0] = win;
+  out[1] = wtot;
+  out[2] = (int64_t)vmax;
+  out[3] = (int64_t)sq;
+  return OR_OK;
 }
 
 int or_sparsify(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,

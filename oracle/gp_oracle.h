@@ -34,7 +34,7 @@ typedef struct {
   int32_t lp_rounds, lp_subrounds;  /* clustering LP: 5 rounds x 8 sub-rounds */
   int32_t ref_rounds;               /* refinement LP rounds, 5 */
   int32_t ip_trials;                /* greedy growing trials per bisection, 8 */
-  int32_t sparsifier;               /* 0 none, 1 weighted threshold, 2 uniform */
+  int32_t sparsifier;               /* 0 none, 1 weighted threshold, 2 uniform, 3 exact-count threshold */
   int32_t two_hop, isolated;        /* enable 2-hop / isolated-node clustering */
   int32_t max_levels;               /* hard cap on hierarchy depth */
   int32_t dbg_max_subrounds;        /* <0: unlimited; else stop LP after that many sub-rounds */

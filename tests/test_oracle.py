@@ -473,3 +473,108 @@ def test_determinism():
     assert a.cut == b.cut and (a.blocks == b.blocks).all()
     c = orc.partition(g, 4, 0.03, 10)
     assert not (a.blocks == c.blocks).all()
+
+
+# ------------------------------------------- exact-count threshold sampling
+
+def test_h64_extends_h32():
+    k = orc.key(11, orc.TAG_SPARSE, 3, 0)
+    for x, y in [(0, 1), (5, 77), (123456, 7654321), (2**31 - 2, 2**31 - 1)]:
+        assert orc.h64(k, x, y) >> 32 == orc.h32(k, x, y)
+
+
+@pytest.mark.parametrize("wmax,seed", [(1, 1), (3, 2), (50, 3)])
+def test_exact_count_sampling_keeps_exactly_m_hat(wmax, seed):
+    # mode 3: of the edges of weight omega_t exactly m_hat - |E>| stay, the first ones in the
+    # order of (64-bit hash, min, max); the level then holds exactly m_hat edges
+    g = gg.with_edge_weights(gg.er(3000, 30000, 5), wmax)
+    orig = {e: w for e, w in to_sets(g).items() if e[0] < e[1]}
+    for mh in (1, 100, g.m // 3, g.m - 1):
+        s, st = orc.sparsify(g, mh, 2, seed, mode=3)
+        check_csr(s)
+        kept = {e: w for e, w in to_sets(s).items() if e[0] < e[1]}  # undirected edges
+        assert len(kept) == mh
+        wt = st.omega_t
+        assert all(orig[e] == w and w >= wt for e, w in kept.items())
+        assert {e for e, w in orig.items() if w > wt} <= set(kept)
+        key = orc.key(seed, orc.TAG_SPARSE, 2, 0)
+        order = lambda e: (orc.h64(key, e[0], e[1]), e[0], e[1])
+        eq_kept = [order(e) for e, w in kept.items() if w == wt]
+        eq_dropped = [order(e) for e, w in orig.items() if w == wt and e not in kept]
+        assert len(eq_kept) == mh - st.n_greater
+        if eq_kept and eq_dropped:
+            assert max(eq_kept) < min(eq_dropped)
+        if eq_kept:
+            assert st.threshold == max(eq_kept)[0]
+
+
+def test_partition_with_exact_count_sampling_meets_the_edge_bound():
+    g = gg.er(20000, 100000, 3)
+    r = orc.partition(g, 4, 0.03, 1, orc.Config.default(sparsifier=3))
+    assert r.rc == orc.OK
+    trig = [r.stats.lv[i] for i in range(r.stats.levels) if r.stats.lv[i].triggered]
+    assert trig
+    assert all(L.m_next == L.m_hat for L in trig)
+
+
+# ----------------------------------------------------- modularity (Sec. 5)
+
+def _modularity_direct(g, lab):
+    """Q_C, sum e_ii and alpha_C of Sec. 5 from the edge list, in floating point."""
+    m2 = float(np.asarray(g.adjwgt, dtype=np.float64).sum())
+    rows = row_index(g)
+    w = np.asarray(g.adjwgt, dtype=np.float64)
+    inside = w[lab[rows] == lab[g.adjncy]].sum() / m2
+    vol = np.bincount(lab[rows], weights=w, minlength=lab.max() + 1) / m2
+    return inside - (vol ** 2).sum(), inside, vol.max()
+
+
+def test_modularity_hand_example():
+    # two triangles joined by one edge, one cluster per triangle: e_ii = 3/7, a_i = 1/2,
+    # Q = 2 (3/7 - 1/4) = 5/14
+    g = hand(6, [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (2, 3)])
+    M = orc.modularity(g, np.array([0, 0, 0, 1, 1, 1]), 2)
+    assert (M.w_internal, M.w_total, M.vol_max, M.vol_sq) == (12, 14, 7, 98)
+    assert abs(M.q - 5 / 14) < 1e-15 and abs(M.alpha - 0.5) < 1e-15
+    # one cluster: Q = 1 - 1 = 0; singletons: Q = -sum (d_v / 2m)^2
+    one = orc.modularity(g, np.zeros(6, dtype=np.int32), 1)
+    assert one.q == 0.0 and one.inside == 1.0
+    single = orc.modularity(g, np.arange(6), 6)
+    deg = np.diff(g.xadj)
+    assert abs(single.q + ((deg / 14.0) ** 2).sum()) < 1e-15
+
+
+def test_modularity_matches_networkx():
+    nx = pytest.importorskip("networkx")
+    for g in (gg.er(400, 1600, 2), gg.with_edge_weights(gg.er(300, 1500, 4), 9), gg.grid2d(20, 15)):
+        lab, _, _ = orc.cluster(g, 8, 1, 3)
+        _, lab = np.unique(lab, return_inverse=True)
+        M = orc.modularity(g, lab, int(lab.max()) + 1)
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        rows = row_index(g)
+        for u, v, w in zip(rows.tolist(), g.adjncy.tolist(), g.adjwgt.tolist()):
+            if u < v:
+                G.add_edge(u, v, weight=w)
+        comms = [set(np.flatnonzero(lab == c).tolist()) for c in range(int(lab.max()) + 1)]
+        assert abs(M.q - nx.community.modularity(G, comms, weight="weight")) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_modularity_lemma2_bounds(seed):
+    # Lemma 2: Q_C <= sum_i e_ii <= Q_C + alpha_C, on LP clusterings and random ones
+    g = gg.with_edge_weights(gg.er(2000, 12000, seed), 5)
+    rng = np.random.default_rng(seed)
+    lab_lp, _, _ = orc.cluster(g, 30, 1, seed)
+    for lab in (np.unique(lab_lp, return_inverse=True)[1], rng.integers(0, 7, g.n), rng.integers(0, 500, g.n)):
+        M = orc.modularity(g, lab, int(lab.max()) + 1)
+        q, inside, alpha = _modularity_direct(g, lab)
+        assert abs(M.q - q) < 1e-12 and abs(M.inside - inside) < 1e-12 and abs(M.alpha - alpha) < 1e-12
+        assert M.q <= M.inside + 1e-15 <= M.q + M.alpha + 2e-15
+        assert 1 - M.inside >= M.bound - 1e-15  # the between-cluster fraction exceeds the bound
+
+
+def test_modularity_rejects_labels_out_of_range():
+    g = gg.er(100, 300, 1)
+    with pytest.raises(RuntimeError):
+        orc.modularity(g, np.full(g.n, 3), 3)
