@@ -318,6 +318,15 @@ def run_gpu(args, world, rank, local):
     ctx.profile(False)
     prof = ctx.profile_read()
     profiled_ms = pv0.elapsed_time(pv1) / args.steps
+    # Sec. 5 diagnostic of the level-1 clustering (outside the timed steps)
+    U1 = st.U
+    cmap1, nc1, _ = ctx.gp_coarsen(dg, U1, 1, w["seed"])
+    mod = ctx.gp_modularity(dg, cmap1, nc1).as_dict()
+    L1 = st.levels_list()[0] if st.levels else None
+    if L1:
+        mod["kept_edge_fraction"] = L1["m_coarse"] / L1["m"]
+        mod["what"] = ("Q_C, alpha_C and Lemma 2's bound 1 - Q_C - alpha_C for the level-1 clustering; "
+                       "kept_edge_fraction = coarse edges / input edges before sparsification")
     coarsen_ms = sum(s[0] for s in stats)
     if world > 1:
         t = torch.tensor([step_ms, coarsen_ms], dtype=torch.float64, device="cuda")
@@ -402,7 +411,7 @@ def run_gpu(args, world, rank, local):
             "hierarchy": {"columns": ["n", "m", "n_next", "m_coarse", "m_hat", "triggered", "m_next"],
                           "levels": hierarchy},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches // max(args.steps, 1),
-            "gpu_launches_total": launches, "clocks": clk,
+            "gpu_launches_total": launches, "clocks": clk, "modularity_level1": mod,
             "kernel_classes_from": "a second pass over the same steps with per-class CUDA events "
                                    f"({profiled_ms:.1f} ms per step with the events)",
             "kernel_classes": {k: v for k, v in prof.items() if v["launches"]}}
@@ -457,6 +466,37 @@ def run_level1(args):
     return 0
 
 
+def run_report(args):
+    """Per-level nodes and edges of the hierarchy with each sparsifier (Sec. 4.2; the synthetic
+    analogue of the paper's edges-per-level figure), with cut and phase times."""
+    import torch
+    import paper_2504_17615_gb300 as gp
+    from paper_2504_17615_gb300 import build as gpbuild
+    w = workload_of(args)
+    gpbuild.build()
+    g = make_graph(w, 0, 1)
+    ctx = gp.Context(0)
+    dg = gp.DeviceGraph.from_host(g)
+    out = {"report": "hierarchy by sparsifier", "config": {"workload": w["name"], "k": w["k"], "eps": w["eps"],
+                                                        "seed": w["seed"]}, "modes": {}}
+    names = {gp.GP_SPARSIFY_NONE: "none", gp.GP_SPARSIFY_TWEIGHT: "t_weight", gp.GP_SPARSIFY_UNIFORM: "uniform",
+             gp.GP_SPARSIFY_TWEIGHT_EXACT: "t_weight_exact"}
+    for mode, name in names.items():
+        cfg = gp.default_config(sparsifier=mode)
+        ctx.gp_partition(dg, w["k"], w["eps"], w["seed"], cfg)  # warm-up
+        torch.cuda.synchronize()
+        _, cut, st = ctx.gp_partition(dg, w["k"], w["eps"], w["seed"], cfg)
+        levels = [{"n": L["n"], "m": L["m"], "m_coarse": L["m_coarse"], "m_hat": L["m_hat"],
+                   "triggered": L["triggered"], "m_next": L["m_next"]} for L in st.levels_list()]
+        out["modes"][name] = {"cut": cut, "ms_total": st.ms_total, "ms_coarsen": st.ms_coarsen,
+                              "levels": levels, "n_coarsest": st.n_coarsest,
+                              "edges_summed_over_levels": sum(L["m"] for L in levels)}
+        log(f"[bench] report {name}: cut={cut} total {st.ms_total:.1f} ms coarsen {st.ms_coarsen:.1f} ms")
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,6 +508,8 @@ def main():
                     help="ER graph with 2^S nodes and average degree 20 instead (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--report", action="store_true",
+                    help="per-level hierarchy of the workload with each sparsifier (no timing contract)")
     ap.add_argument("--level1", action="store_true",
                     help="time level 1 of Alg. 1 alone on the workload graph (profiling case)")
     ap.add_argument("--traffic", type=float, default=None,
@@ -480,6 +522,8 @@ def main():
         return run_reference(args, world, rank)
     if args.level1:
         return run_level1(args)
+    if args.report:
+        return run_report(args)
     return run_gpu(args, world, rank, local)
 
 

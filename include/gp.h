@@ -63,8 +63,8 @@ typedef struct gp_allocator {
   void *user;
 } gp_allocator;
 
-/* Sparsifier choice (Sec. 4.2). */
-enum { GP_SPARSIFY_NONE = 0, GP_SPARSIFY_TWEIGHT = 1, GP_SPARSIFY_UNIFORM = 2 };
+/* Sparsifier choice (Sec. 4.2; the exact-count variant keeps exactly m_hat edges). */
+enum { GP_SPARSIFY_NONE = 0, GP_SPARSIFY_TWEIGHT = 1, GP_SPARSIFY_UNIFORM = 2, GP_SPARSIFY_TWEIGHT_EXACT = 3 };
 
 /*
  * Method parameters.  gp_config_default() gives the paper's values:
@@ -160,11 +160,15 @@ gp_status gp_contract(gp_ctx *ctx, const gp_graph *g, const int32_t *cmap, int32
  * undirected edge weight w_t is found; heavier edges are kept, lighter ones
  * dropped and edges of weight w_t kept with probability
  * (m_hat - |E>|) / |E=| by a counter-based hash of their endpoints.
- * GP_SPARSIFY_UNIFORM keeps every edge with probability m_hat / |E|.  Kept
- * edges keep their weights; node weights are copied.  *out is allocated
- * through the context allocator.  `stats` (host, may be NULL) gets w_t,
- * |E>|, |E=| and the hash threshold in its omega_t / n_greater / n_equal /
- * threshold fields.  Synchronises.
+ * GP_SPARSIFY_UNIFORM keeps every edge with probability m_hat / |E|.
+ * GP_SPARSIFY_TWEIGHT_EXACT selects w_t in the same way but keeps, of the
+ * edges of weight w_t, exactly m_hat - |E>|: those first in the order of
+ * (64-bit hash of the endpoints, smaller endpoint, larger endpoint), so the
+ * result has exactly min(m_hat, |E|) edges.  Kept edges keep their weights;
+ * node weights are copied.  *out is allocated through the context allocator.
+ * `stats` (host, may be NULL) gets w_t, |E>|, |E=| and the hash threshold
+ * (the last kept hash in the exact mode) in its omega_t / n_greater /
+ * n_equal / threshold fields.  Synchronises.
  */
 gp_status gp_sparsify(gp_ctx *ctx, const gp_graph *g, int64_t m_hat, int32_t level,
                       uint64_t seed, int32_t mode, gp_graph *out, gp_level_stats *stats);
@@ -266,6 +270,31 @@ void gp_profile_reset(gp_ctx *ctx);
 int gp_profile_count(void);
 const char *gp_profile_name(int i);
 gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, double *bytes);
+
+/*
+ * Modularity of a clustering (Sec. 5).  With e_ij the fraction of the edge
+ * weight running from cluster i to cluster j (both directions of an edge
+ * counted, so the fractions sum to one), a_i = sum_j e_ij, Q_C = sum_i (e_ii -
+ * a_i^2) and alpha_C = max_i a_i, Lemma 2 bounds the weight fraction inside
+ * the clusters by Q_C <= sum_i e_ii <= Q_C + alpha_C: 1 - Q_C - alpha_C is a
+ * lower bound of the fraction of the weight that a contraction of the
+ * clustering keeps (before parallel edges merge), the paper's criterion for
+ * whether sparsification will be needed.  labels (device, g->n entries) must
+ * lie in [0, nlabels) (else GP_ERR_INVALID).  The integer totals are exact;
+ * the fractions are computed from them in double precision.  Synchronises.
+ */
+typedef struct gp_modularity_stats {
+  int64_t w_internal;  /* sum over CSR entries whose endpoints share a cluster */
+  int64_t w_total;     /* sum over all CSR entries (twice the edge weight) */
+  int64_t vol_max;     /* largest cluster volume (sum of its nodes' weighted degrees) */
+  uint64_t vol_sq;     /* sum of squared cluster volumes */
+  double inside;       /* sum_i e_ii = w_internal / w_total */
+  double q;            /* Q_C */
+  double alpha;        /* alpha_C */
+  double bound;        /* 1 - Q_C - alpha_C */
+} gp_modularity_stats;
+gp_status gp_modularity(gp_ctx *ctx, const gp_graph *g, const int32_t *labels, int32_t nlabels,
+                        gp_modularity_stats *out);
 
 /*
  * Measurement helper with no counterpart in the paper: the device's rate of

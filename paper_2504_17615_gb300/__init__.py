@@ -21,7 +21,7 @@ _lib = None
 
 GP_OK, GP_ERR_INVALID, GP_ERR_INFEASIBLE, GP_ERR_OVERFLOW = 0, 1, 2, 3
 GP_ERR_OOM, GP_ERR_CUDA, GP_ERR_TIMEOUT, GP_ERR_BUDGET = 4, 5, 6, 7
-GP_SPARSIFY_NONE, GP_SPARSIFY_TWEIGHT, GP_SPARSIFY_UNIFORM = 0, 1, 2
+GP_SPARSIFY_NONE, GP_SPARSIFY_TWEIGHT, GP_SPARSIFY_UNIFORM, GP_SPARSIFY_TWEIGHT_EXACT = 0, 1, 2, 3
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID", 2: "GP_ERR_INFEASIBLE", 3: "GP_ERR_OVERFLOW",
                 4: "GP_ERR_OOM", 5: "GP_ERR_CUDA", 6: "GP_ERR_TIMEOUT", 7: "GP_ERR_BUDGET"}
 
@@ -66,6 +66,15 @@ class gp_level_stats(ctypes.Structure):
                 ("threshold", ctypes.c_uint64), ("lp_subrounds", ctypes.c_int32),
                 ("lp_moves", ctypes.c_int64), ("clusters_lp", ctypes.c_int64),
                 ("clusters_2hop", ctypes.c_int64), ("clusters_final", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class gp_modularity_stats(ctypes.Structure):
+    _fields_ = [("w_internal", ctypes.c_int64), ("w_total", ctypes.c_int64), ("vol_max", ctypes.c_int64),
+                ("vol_sq", ctypes.c_uint64), ("inside", ctypes.c_double), ("q", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("bound", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -129,6 +138,7 @@ def _load():
             "gp_profile_read": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(d),
                                                ctypes.POINTER(d)]),
             "gp_measure_random_reads": (ctypes.c_int, [P, i64, i64, ctypes.POINTER(d)]),
+            "gp_modularity": (ctypes.c_int, [P, ctypes.POINTER(gp_graph), P, i32, ctypes.POINTER(gp_modularity_stats)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -424,6 +434,14 @@ class Context:
             out[self.lib.gp_profile_name(i).decode()] = {"launches": la.value, "ms": ms.value,
                                                          "bytes": by.value}
         return out
+
+    def gp_modularity(self, g, labels, nlabels: int) -> gp_modularity_stats:
+        """Sec. 5 modularity of a clustering given as device labels in [0, nlabels)."""
+        st = gp_modularity_stats()
+        s = g.struct()
+        self._check(self.lib.gp_modularity(self.ptr, ctypes.byref(s), ctypes.c_void_p(labels.data_ptr()),
+                                           nlabels, ctypes.byref(st)))
+        return st
 
     def measure_random_reads(self, array_bytes: int, reads: int) -> float:
         """Random 4-byte reads per second from an array of array_bytes bytes."""

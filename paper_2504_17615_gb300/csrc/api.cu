@@ -349,6 +349,16 @@ gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, dou
   });
 }
 
+gp_status gp_modularity(gp_ctx *ctx, const gp_graph *g, const int32_t *labels, int32_t nlabels,
+                        gp_modularity_stats *out) {
+  return guarded(ctx, [&] {
+    GP_REQUIRE(g && out, GP_ERR_INVALID, "null argument");
+    gp::DevGraph dg = gp::DevGraph::wrap(*g);
+    gp::validate_graph(ctx, dg, false);
+    gp::modularity(ctx, dg, labels, nlabels, out);
+  });
+}
+
 gp_status gp_measure_random_reads(gp_ctx *ctx, int64_t array_bytes, int64_t reads, double *reads_per_s) {
   return guarded(ctx, [&] {
     GP_REQUIRE(reads_per_s, GP_ERR_INVALID, "null output");

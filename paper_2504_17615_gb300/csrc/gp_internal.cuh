@@ -235,6 +235,9 @@ __host__ __device__ __forceinline__ uint64_t stream_key(uint64_t seed, uint32_t 
   return fmix(fmix(seed ^ kGold) + w);
 }
 
+__host__ __device__ __forceinline__ uint64_t h64(uint64_t key, uint32_t x, uint32_t y) {
+  return fmix(key ^ (((uint64_t)x << 32) | (uint64_t)y));
+}
 __host__ __device__ __forceinline__ uint32_t h32(uint64_t key, uint32_t x, uint32_t y) {
   return (uint32_t)(fmix(key ^ (((uint64_t)x << 32) | (uint64_t)y)) >> 32);
 }
@@ -396,6 +399,7 @@ struct GraphTotals {
 GraphTotals validate_graph(gp_ctx *ctx, const DevGraph &g, bool full);
 int64_t lmax_of(int64_t W, int32_t k, int64_t eps_ppm);
 double measure_random_reads(gp_ctx *ctx, int64_t array_bytes, int64_t reads);
+void modularity(gp_ctx *ctx, const DevGraph &g, const int32_t *labels, int32_t nlabels, gp_modularity_stats *out);
 void check_blocks(gp_ctx *ctx, const int32_t *blocks, int n, int k);
 void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, uint64_t seed,
                     const gp_config &cfg, int32_t *blocks, int64_t *cut_out, gp_partition_stats *st);

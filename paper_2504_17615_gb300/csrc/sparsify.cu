@@ -19,6 +19,9 @@
 // rows contiguously from the first row's new offset.
 #include "gp_internal.cuh"
 
+#include <algorithm>
+#include <utility>
+
 namespace gp {
 
 namespace {
@@ -52,10 +55,11 @@ __global__ void k_whist(const int32_t *__restrict__ w, int64_t m2, int cap_mode,
 struct KeepArgs {
   const int32_t *xadj, *adjncy, *adjwgt;
   int n;
-  int mode;  // 0 keep none, 1 threshold, 2 uniform, 3 keep all
+  int mode;  // 0 keep none, 1 threshold, 2 uniform, 3 keep all, 4 exact-count threshold
   int32_t wt;
-  uint64_t T;
+  uint64_t T;   // modes 1, 2: 32-bit hash threshold; mode 4: the last kept 64-bit hash
   uint64_t key;
+  uint32_t blo, bhi;  // mode 4: the last kept edge among those whose hash equals T
   int32_t *cnt;         // count pass: kept entries per row
   const int32_t *nxadj; // write pass: new row offsets
   int32_t *oadj, *ow;
@@ -67,6 +71,11 @@ __device__ __forceinline__ bool keep_entry(const KeepArgs &a, int row, int v, in
   if (a.mode == 3) return true;
   if (a.mode == 0) return false;
   const uint32_t lo = (uint32_t)(row < v ? row : v), hi = (uint32_t)(row < v ? v : row);
+  if (a.mode == 4) {
+    if (x != a.wt) return x > a.wt;
+    const uint64_t h = h64(a.key, lo, hi);
+    return h < a.T || (h == a.T && (lo < a.blo || (lo == a.blo && hi <= a.bhi)));
+  }
   const uint64_t h = h32(a.key, lo, hi);
   if (a.mode == 2) return h < a.T;
   return x > a.wt || (x == a.wt && h < a.T);
@@ -131,6 +140,124 @@ __global__ void __launch_bounds__(256) k_keep(KeepArgs a) {
   }
 }
 
+// Exact-count mode: histogram of one digit of the 64-bit hash of the edges of
+// weight wt (entries with row < neighbour, so every edge once), restricted to
+// the hashes whose bits above the digit equal `prefix`; the same 32-row walk
+// as k_keep.
+struct HashHistArgs {
+  const int32_t *xadj, *adjncy, *adjwgt;
+  int n;
+  int32_t wt;
+  uint64_t key;
+  int above;        // bits above the digit (0: no prefix)
+  uint64_t prefix;
+  int shift, nbits;
+  unsigned long long *hist;
+  uint32_t *pairs;  // collect mode: (lo, hi) of the edges whose hash equals `prefix`
+  int *npairs;
+  int cap;
+};
+
+template <bool COLLECT>
+__global__ void __launch_bounds__(256) k_hash_digit(HashHistArgs a) {
+  __shared__ unsigned s_h[2048];
+  if (!COLLECT) {
+    for (int t = threadIdx.x; t < (1 << a.nbits); t += blockDim.x) s_h[t] = 0;
+    __syncthreads();
+  }
+  const int lane = (int)lane_id();
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int64_t u0 = (int64_t)wid * 32; u0 < a.n; u0 += (int64_t)nw * 32) {
+    const int64_t u = u0 + lane;
+    const int xe = u < a.n ? a.xadj[u + 1] : 0x7FFFFFFF;
+    const int e0 = a.xadj[u0];
+    const int last = (int)((a.n - u0) < 32 ? (a.n - u0) : 32) - 1;
+    const int e1 = __shfl_sync(FULL, xe, last);
+    for (int f0 = e0; f0 < e1; f0 += 32) {
+      const int e = f0 + lane;
+      int q = 0;  // owner: lanes whose row ends at or before e
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int val = __shfl_sync(FULL, xe, q + step - 1);
+        if (val <= e) q += step;
+      }
+      if (e >= e1) continue;
+      const int row = (int)(u0 + q), v = __ldcs(a.adjncy + e);
+      if (row >= v || __ldcs(a.adjwgt + e) != a.wt) continue;
+      const uint64_t h = h64(a.key, (uint32_t)row, (uint32_t)v);
+      if (COLLECT) {
+        if (h == a.prefix) {
+          const int j = atomicAdd(a.npairs, 1);
+          if (j < a.cap) { a.pairs[2 * j] = (uint32_t)row; a.pairs[2 * j + 1] = (uint32_t)v; }
+        }
+      } else {
+        if (a.above > 0 && (h >> (64 - a.above)) != a.prefix) continue;
+        atomicAdd(&s_h[(unsigned)(h >> a.shift) & ((1u << a.nbits) - 1u)], 1u);
+      }
+    }
+  }
+  if (!COLLECT) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < (1 << a.nbits); t += blockDim.x)
+      if (s_h[t]) atomicAdd(&a.hist[t], (unsigned long long)s_h[t]);
+  }
+}
+
+// The r-th smallest (1-based) 64-bit hash among the edges of weight wt, and the
+// edge that closes the kept prefix when several edges share that hash.
+void exact_boundary(gp_ctx *ctx, const DevGraph &g, int32_t wt, uint64_t key, int64_t r, uint64_t *t_out,
+                    uint32_t *blo, uint32_t *bhi) {
+  const int digits[6][2] = {{53, 11}, {42, 11}, {31, 11}, {20, 11}, {10, 10}, {0, 10}};  // (shift, bits)
+  DBuf<unsigned long long> hist(ctx, 2048);
+  std::vector<unsigned long long> h(2048);
+  HashHistArgs a{g.xadj, g.adjncy, g.adjwgt, g.n, wt, key, 0, 0, 0, 0, hist.get(), nullptr, nullptr, 0};
+  const int grid = grid_for(g.n, 256, ctx->num_sms * 16);
+  uint64_t prefix = 0;
+  int64_t below = 0, equal = 0;
+  for (int d = 0; d < 6; d++) {
+    a.shift = digits[d][0];
+    a.nbits = digits[d][1];
+    a.prefix = prefix;
+    a.above = 64 - (digits[d][0] + digits[d][1]);
+    hist.zero();
+    k_hash_digit<false><<<grid, 256, 0, ctx->stream>>>(a);
+    GP_LAUNCH_CHECK();
+    const int nb = 1 << a.nbits;
+    read_back(ctx, hist.get(), sizeof(unsigned long long) * nb, h.data());
+    int b = 0;
+    for (; b < nb - 1; b++) {
+      if (below + (int64_t)h[b] >= r) break;
+      below += (int64_t)h[b];
+    }
+    prefix = (prefix << a.nbits) | (uint64_t)b;
+    equal = (int64_t)h[b];
+  }
+  *t_out = prefix;
+  *blo = 0xFFFFFFFFu;
+  *bhi = 0xFFFFFFFFu;
+  const int64_t need = r - below;  // edges with hash == prefix to keep, 1 <= need <= equal
+  if (need < equal) {  // a 64-bit hash collision inside E=: order the tied edges by their endpoints
+    GP_REQUIRE(equal <= (1 << 20), GP_ERR_INVALID, "too many equal hashes in the exact sampler");
+    DBuf<uint32_t> pairs(ctx, (size_t)(2 * equal));
+    DBuf<int> np(ctx, 1);
+    np.zero();
+    a.prefix = prefix;
+    a.pairs = pairs.get();
+    a.npairs = np.get();
+    a.cap = (int)equal;
+    k_hash_digit<true><<<grid, 256, 0, ctx->stream>>>(a);
+    GP_LAUNCH_CHECK();
+    std::vector<uint32_t> hp((size_t)(2 * equal));
+    read_back(ctx, pairs.get(), sizeof(uint32_t) * 2 * equal, hp.data());
+    std::vector<std::pair<uint32_t, uint32_t>> ps;
+    for (int64_t i = 0; i < equal; i++) ps.emplace_back(hp[2 * i], hp[2 * i + 1]);
+    std::sort(ps.begin(), ps.end());
+    *blo = ps[(size_t)need - 1].first;
+    *bhi = ps[(size_t)need - 1].second;
+  }
+}
+
 // Selects the entry of descending rank R (1-based) among the weights with a
 // three-digit MSD radix select; returns the value and the counts above/equal.
 int32_t radix_select_desc(gp_ctx *ctx, const int32_t *w, int64_t m2, int64_t R, int64_t *above,
@@ -166,8 +293,8 @@ void sparsify_graph(gp_ctx *ctx, const DevGraph &g, int64_t m_hat, int32_t level
                     int mode, DevGraph &out, gp_level_stats *st) {
   ProfScope ps(ctx, PROF_SPARSIFY);
   TraceTimer trace(ctx);
-  GP_REQUIRE(mode == GP_SPARSIFY_TWEIGHT || mode == GP_SPARSIFY_UNIFORM, GP_ERR_INVALID,
-             "unknown sparsifier mode");
+  GP_REQUIRE(mode == GP_SPARSIFY_TWEIGHT || mode == GP_SPARSIFY_UNIFORM || mode == GP_SPARSIFY_TWEIGHT_EXACT,
+             GP_ERR_INVALID, "unknown sparsifier mode");
   const int n = g.n;
   const int64_t m2 = g.m2, m = m2 / 2;
   int kmode;
@@ -209,7 +336,12 @@ void sparsify_graph(gp_ctx *ctx, const DevGraph &g, int64_t m_hat, int32_t level
   }
   const uint64_t key = stream_key(seed, mode == GP_SPARSIFY_UNIFORM ? TAG_UNIFORM : TAG_SPARSE,
                                   (uint32_t)level, 0);
-  KeepArgs a{g.xadj, g.adjncy, g.adjwgt, n, kmode, wt, T, key, nullptr, nullptr, nullptr, nullptr};
+  uint32_t blo = 0, bhi = 0;
+  if (kmode == 1 && mode == GP_SPARSIFY_TWEIGHT_EXACT) {
+    kmode = 4;
+    exact_boundary(ctx, g, wt, key, m_hat - ng, &T, &blo, &bhi);
+  }
+  KeepArgs a{g.xadj, g.adjncy, g.adjwgt, n, kmode, wt, T, key, blo, bhi, nullptr, nullptr, nullptr, nullptr};
   DBuf<int32_t> cnt(ctx, (size_t)n + 1), total(ctx, 1);
   const int kgrid = grid_for(n, 256, ctx->num_sms * 16);
   GP_CUDA(cudaMemsetAsync(cnt.get() + n, 0, sizeof(int32_t), ctx->stream));
@@ -239,7 +371,7 @@ void sparsify_graph(gp_ctx *ctx, const DevGraph &g, int64_t m_hat, int32_t level
     GP_CUDA(cudaMemcpyAsync(out.vwgt, g.vwgt, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   // weights once for the selection (T-Weight only), ids and weights once for the keep test,
   // the kept entries written, row offsets read and written, node weights copied
-  prof_bytes(ctx, PROF_SPARSIFY, (kmode == 1 ? 4.0 * m2 : 0.0) + 8.0 * m2 + 8.0 * m2_out + 8.0 * (n + 1) + 8.0 * n);
+  prof_bytes(ctx, PROF_SPARSIFY, (kmode == 1 || kmode == 4 ? 4.0 * m2 : 0.0) + 8.0 * m2 + 8.0 * m2_out + 8.0 * (n + 1) + 8.0 * n);
   if (trace.on())
     fprintf(stderr, "[gp sparsify] m2=%lld -> %d ms=%.2f\n", (long long)m2, m2_out, trace.ms());
   if (st) {

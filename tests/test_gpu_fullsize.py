@@ -149,6 +149,22 @@ def test_c3_level1_clustering_properties(gp, ctx, c3, c3_level1):
     assert st.clusters_final <= st.clusters_2hop <= st.clusters_lp < g.n
 
 
+def test_c3_level1_modularity(gp, ctx, c3, c3_level1):
+    """Sec. 5 on the level-1 clustering: exact totals against the host, and Lemma 2's bound
+    below the weight fraction the contraction keeps."""
+    import torch
+    g, dg = c3
+    U, cmap, nc, st, cg, h = c3_level1
+    M = ctx.gp_modularity(dg, torch.from_numpy(cmap).cuda(), nc)
+    inter = inter_cluster_weight(g, cmap)
+    assert M.w_total == g.m2 and M.w_internal == g.m2 - inter
+    vol = np.bincount(cmap, weights=np.diff(np.asarray(g.xadj, dtype=np.int64)), minlength=nc).astype(np.int64)
+    assert M.vol_max == int(vol.max())
+    assert M.vol_sq == int((vol * vol).sum())
+    assert M.q <= M.inside <= M.q + M.alpha  # Lemma 2
+    assert int(np.asarray(h.adjwgt, dtype=np.int64).sum()) / g.m2 >= M.bound
+
+
 def test_c3_level1_contraction_sampled(gp, ctx, c3, c3_level1):
     g, _ = c3
     U, cmap, nc, st, cg, h = c3_level1

@@ -158,7 +158,7 @@ def test_contract_matches_oracle(gp, ctx, name):
 # ----------------------------------------------------------- sparsification
 
 @pytest.mark.parametrize("wmax", [1, 5, 100000])
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_sparsify_matches_oracle(gp, ctx, wmax, mode):
     g = gg.with_edge_weights(gg.er(4000, 50000, 6), wmax)
     dg = gp.DeviceGraph.from_host(g)
@@ -293,7 +293,7 @@ def test_partition_matches_oracle(gp, ctx, name, k):
     _check_partition(gp, ctx, GRAPHS[name], k, 0.03, 2)
 
 
-@pytest.mark.parametrize("kw", [{"sparsifier": 0}, {"sparsifier": 2}, {"ref_rounds": 0},
+@pytest.mark.parametrize("kw", [{"sparsifier": 0}, {"sparsifier": 2}, {"sparsifier": 3}, {"ref_rounds": 0},
                                 {"coarsest_factor": 20}, {"ip_trials": 1}])
 def test_partition_config_variants(gp, ctx, kw):
     _check_partition(gp, ctx, gg.er(20000, 100000, 3), 4, 0.05, 4, kw)
@@ -367,3 +367,33 @@ def test_partition_through_torch_allocator(gp):
         assert cut == r.cut and np.array_equal(blocks.cpu().numpy(), r.blocks)
     finally:
         c.close()
+
+
+# ------------------------------------------------------- modularity (Sec. 5)
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_modularity_matches_oracle(gp, ctx, name):
+    import torch
+    g = GRAPHS[name]
+    rng = np.random.default_rng(4)
+    lab_lp, _, _ = orc.cluster(g, 12, 1, 2)
+    cases = [np.unique(lab_lp, return_inverse=True)[1], np.zeros(g.n, dtype=np.int64),
+             np.arange(g.n), rng.integers(0, 37, g.n)]
+    dg = gp.DeviceGraph.from_host(g)
+    for lab in cases:
+        nl = int(lab.max()) + 1
+        st = ctx.gp_modularity(dg, torch.from_numpy(lab.astype(np.int32)).cuda(), nl)
+        M = orc.modularity(g, lab, nl)
+        assert (st.w_internal, st.w_total, st.vol_max, st.vol_sq) == (M.w_internal, M.w_total, M.vol_max, M.vol_sq)
+        for f in ("inside", "q", "alpha", "bound"):
+            assert abs(getattr(st, f) - getattr(M, f)) <= 1e-12, f
+
+
+def test_modularity_rejects_labels_out_of_range(gp, ctx):
+    import torch
+    g = GRAPHS["er"]
+    dg = gp.DeviceGraph.from_host(g)
+    lab = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    lab[17] = 5
+    with pytest.raises(gp.GpError):
+        ctx.gp_modularity(dg, lab, 5)
