@@ -466,6 +466,72 @@ def run_level1(args):
     return 0
 
 
+def batch_mix(count, nmax, seed):
+    """Independent graphs of the batched workload: n log-uniform in [1e3, nmax], the generator
+    uniform over ER (average degree 8..32), 2D grid, 3D grid and R-MAT (edge factor 8), unit
+    weights, k uniform over {2, 4, ..., 64}, eps 0.03, a seed per graph."""
+    import numpy as np
+    import graphgen as gg
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(nmax))))
+        kind = int(rng.integers(0, 4))
+        if kind == 0:
+            g = gg.er(n, n * int(rng.integers(4, 17)), int(rng.integers(1, 1 << 30)))
+        elif kind == 1:
+            s2 = max(2, int(np.sqrt(n)))
+            g = gg.grid2d(s2, s2)
+        elif kind == 2:
+            s3 = max(2, int(round(n ** (1 / 3))))
+            g = gg.grid3d(s3, s3, s3)
+        else:
+            g = gg.rmat(max(10, int(round(np.log2(n)))), 8, seed=int(rng.integers(1, 1 << 30)))
+        jobs.append((g, int(2 ** rng.integers(1, 7)), 0.03, int(rng.integers(1, 1 << 30))))
+    return jobs
+
+
+def run_batch(args):
+    """Batched form: the same graphs one gp_partition call after another, then all at once through
+    gp_partition_batch; graphs/s of both, and the results must agree item by item."""
+    import numpy as np
+    import torch
+    import paper_2504_17615_gb300 as gp
+    from paper_2504_17615_gb300 import build as gpbuild
+    gpbuild.build()
+    t = time.time()
+    jobs = batch_mix(args.batch_count, args.batch_nmax, 1)
+    log(f"[bench] generated {len(jobs)} graphs in {time.time() - t:.1f}s")
+    ctx = gp.Context(0)
+    dev = [(gp.DeviceGraph.from_host(g), k, e, sd) for g, k, e, sd in jobs]
+    torch.cuda.synchronize()
+    serial = batched = None
+    for rep in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        ser = [ctx.gp_partition(dg, k, e, sd)[:2] for dg, k, e, sd in dev]
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t
+        t = time.perf_counter()
+        bat = ctx.gp_partition_batch(dev, workers=args.batch_workers)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t
+        if rep >= args.warmup:
+            serial = ts if serial is None else min(serial, ts)
+            batched = tb if batched is None else min(batched, tb)
+    same = all(c1 == c2 and torch.equal(b1, b2) for (b1, c1), (b2, c2) in zip(ser, bat))
+    edges = sum(g.m for g, _, _, _ in jobs)
+    print(json.dumps({"metric": "batched graphs/s", "value": len(jobs) / batched, "unit": "graphs/s",
+                      "serial_graphs_per_s": len(jobs) / serial, "speedup": serial / batched,
+                      "identical_results": same, "graphs": len(jobs), "edges": edges,
+                      "workers": args.batch_workers, "steps": args.steps, "warmup": args.warmup,
+                      "timing": "best of the timed repetitions, host wall clock around each pass",
+                      "config": {"workload": f"{len(jobs)} graphs, n log-uniform in [1e3, {args.batch_nmax:g}], "
+                                             "ER deg 8-32 / 2D grid / 3D grid / R-MAT ef 8, k in {2..64}, eps 0.03"}}),
+          flush=True)
+    ctx.close()
+    return 0
+
+
 def run_report(args):
     """Per-level nodes and edges of the hierarchy with each sparsifier (Sec. 4.2; the synthetic
     analogue of the paper's edges-per-level figure), with cut and phase times."""
@@ -508,6 +574,11 @@ def main():
                     help="ER graph with 2^S nodes and average degree 20 instead (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="batched form: many independent graphs, serial calls against gp_partition_batch")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-nmax", type=float, default=1e5)
+    ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--report", action="store_true",
                     help="per-level hierarchy of the workload with each sparsifier (no timing contract)")
     ap.add_argument("--level1", action="store_true",
@@ -524,6 +595,8 @@ def main():
         return run_level1(args)
     if args.report:
         return run_report(args)
+    if args.batch:
+        return run_batch(args)
     return run_gpu(args, world, rank, local)
 
 

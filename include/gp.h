@@ -272,6 +272,32 @@ const char *gp_profile_name(int i);
 gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, double *bytes);
 
 /*
+ * Many independent graphs partitioned at once (no counterpart in the paper:
+ * a throughput form of gp_partition for batches of small or mid-sized
+ * graphs, whose levels are too small to fill the GPU one graph at a time).
+ * `workers` host threads (1..64), each with its own stream and memory pool
+ * kept in the context, take the items largest first and run the same
+ * partition as gp_partition on each, so every item's blocks and cut equal
+ * those of a gp_partition call with the same arguments.  Work already queued
+ * on the context stream is waited for first.  Per item: `blocks` (device,
+ * g.n entries, caller-owned) and, on return, `cut` and `status` (the item's
+ * own result; its message is lost).  Returns GP_OK when every item succeeded,
+ * else the first failing item's status (gp_last_error names the item).
+ * Synchronises.
+ */
+typedef struct gp_batch_item {
+  gp_graph g;
+  int32_t k;
+  double eps;
+  uint64_t seed;
+  int32_t *blocks;
+  int64_t cut;
+  gp_status status;
+} gp_batch_item;
+gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32_t count, int32_t workers,
+                             const gp_config *cfg);
+
+/*
  * Modularity of a clustering (Sec. 5).  With e_ij the fraction of the edge
  * weight running from cluster i to cluster j (both directions of an edge
  * counted, so the fractions sum to one), a_i = sum_j e_ij, Q_C = sum_i (e_ii -

@@ -39,6 +39,11 @@ class gp_graph(ctypes.Structure):
                 ("adjncy", ctypes.c_void_p), ("vwgt", ctypes.c_void_p), ("adjwgt", ctypes.c_void_p)]
 
 
+class gp_batch_item(ctypes.Structure):
+    _fields_ = [("g", gp_graph), ("k", ctypes.c_int32), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("blocks", ctypes.c_void_p), ("cut", ctypes.c_int64), ("status", ctypes.c_int)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -138,6 +143,7 @@ def _load():
             "gp_profile_read": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(d),
                                                ctypes.POINTER(d)]),
             "gp_measure_random_reads": (ctypes.c_int, [P, i64, i64, ctypes.POINTER(d)]),
+            "gp_partition_batch": (ctypes.c_int, [P, ctypes.POINTER(gp_batch_item), i32, i32, C]),
             "gp_modularity": (ctypes.c_int, [P, ctypes.POINTER(gp_graph), P, i32, ctypes.POINTER(gp_modularity_stats)]),
         }
         for name, (res, args) in sig.items():
@@ -363,6 +369,25 @@ class Context:
                                           ctypes.byref(cfg) if cfg is not None else None,
                                           blocks.data_ptr(), ctypes.byref(cut), ctypes.byref(st)))
         return blocks[:g.n], cut.value, st
+
+    def gp_partition_batch(self, jobs, workers: int = 8, cfg: gp_config | None = None, check: bool = True):
+        """jobs: list of (graph, k, eps, seed).  Returns [(blocks tensor, cut)] in job order
+        ([(blocks, cut, status)] without raising when check is False)."""
+        torch = self.torch
+        arr = (gp_batch_item * max(len(jobs), 1))()
+        outs = []
+        for i, (g, k, eps, seed) in enumerate(jobs):
+            b = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+            outs.append(b)
+            arr[i].g = g.struct()
+            arr[i].k, arr[i].eps, arr[i].seed = k, eps, seed
+            arr[i].blocks = b.data_ptr()
+        st = self.lib.gp_partition_batch(self.ptr, arr, len(jobs), workers,
+                                         ctypes.byref(cfg) if cfg is not None else None)
+        if not check:
+            return [(outs[i][:jobs[i][0].n], arr[i].cut, arr[i].status) for i in range(len(jobs))]
+        self._check(st)
+        return [(outs[i][:jobs[i][0].n], arr[i].cut) for i in range(len(jobs))]
 
     def gp_partition_host(self, n: int, m2: int, xadj, adjncy, vwgt, adjwgt, k: int, eps: float,
                           seed: int, cfg: gp_config | None = None, blocks=None):

@@ -119,6 +119,12 @@ gp_status gp_create(gp_ctx **out, int device, void *stream, const gp_allocator *
 void gp_destroy(gp_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  for (gp_ctx *w : ctx->workers) {
+    cudaStream_t s = w->stream;
+    gp_destroy(w);
+    cudaStreamDestroy(s);
+  }
+  ctx->workers.clear();
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
   for (auto &r : ctx->pending) {
     cudaEventDestroy(r.a);

@@ -107,6 +107,7 @@ struct gp_ctx {
   int64_t prof_launches[gp::PROF_COUNT_] = {};
   unsigned long long *d_units = nullptr;  // PROF_COUNT_ x PROF_UNITS
   double prof_host_bytes[gp::PROF_COUNT_] = {};  // algorithmic bytes of classes sized on the host
+  std::vector<gp_ctx *> workers;                 // batch workers (own streams and pools)
 };
 
 namespace gp {
