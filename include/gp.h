@@ -298,6 +298,45 @@ gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32_t count, i
                              const gp_config *cfg);
 
 /*
+ * Serving (no counterpart in the paper): a request loop for partition
+ * requests that arrive over time.  `workers` host threads (1..64), each with
+ * its own context, stream and memory pool, take queued requests in arrival
+ * order as soon as a worker is free and the request's estimated device
+ * memory fits the budget next to the requests in flight (the first queued
+ * request that fits goes first; a request alone in the server is always
+ * admitted).  Requests in flight overlap on the GPU.  Each request is the
+ * host-array partition of gp_partition_host, so its blocks and cut equal a
+ * gp_partition_host call with the same arguments, alone or in any mix.
+ * The estimate is 4x the request's CSR bytes plus 64 bytes per node plus
+ * 64 MiB; a request whose estimate exceeds the budget is refused at submit
+ * with GP_ERR_BUDGET.  A worker's pool is trimmed back to 1/workers of the
+ * budget after each request.
+ */
+typedef struct gp_server gp_server;
+typedef struct gp_request {
+  int32_t n;
+  int64_t m2;
+  const int32_t *xadj, *adjncy, *vwgt, *adjwgt; /* host arrays, untouched until the request completes */
+  int32_t k;
+  double eps;
+  uint64_t seed;
+  int32_t *blocks;                              /* host output, n entries */
+} gp_request;
+typedef struct gp_response {
+  gp_status status;
+  int64_t cut;
+  double queued_ms, run_ms, total_ms; /* submit to start, start to end, submit to end */
+} gp_response;
+gp_status gp_server_create(gp_server **out, int device, int32_t workers, int64_t hbm_budget_bytes,
+                           const gp_config *cfg);
+/* Queues a request; *ticket identifies it for gp_server_wait. */
+gp_status gp_server_submit(gp_server *srv, const gp_request *req, int64_t *ticket);
+/* Blocks until the request is done, fills *out and forgets the ticket. */
+gp_status gp_server_wait(gp_server *srv, int64_t ticket, gp_response *out);
+/* Finishes the queued and running requests, then stops the workers. */
+void gp_server_destroy(gp_server *srv);
+
+/*
  * Modularity of a clustering (Sec. 5).  With e_ij the fraction of the edge
  * weight running from cluster i to cluster j (both directions of an edge
  * counted, so the fractions sum to one), a_i = sum_j e_ij, Q_C = sum_i (e_ii -

@@ -44,6 +44,18 @@ class gp_batch_item(ctypes.Structure):
                 ("blocks", ctypes.c_void_p), ("cut", ctypes.c_int64), ("status", ctypes.c_int)]
 
 
+class gp_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m2", ctypes.c_int64), ("xadj", ctypes.c_void_p),
+                ("adjncy", ctypes.c_void_p), ("vwgt", ctypes.c_void_p), ("adjwgt", ctypes.c_void_p),
+                ("k", ctypes.c_int32), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("blocks", ctypes.c_void_p)]
+
+
+class gp_response(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cut", ctypes.c_int64), ("queued_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -144,6 +156,10 @@ def _load():
                                                ctypes.POINTER(d)]),
             "gp_measure_random_reads": (ctypes.c_int, [P, i64, i64, ctypes.POINTER(d)]),
             "gp_partition_batch": (ctypes.c_int, [P, ctypes.POINTER(gp_batch_item), i32, i32, C]),
+            "gp_server_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, i32, i64, C]),
+            "gp_server_submit": (ctypes.c_int, [P, ctypes.POINTER(gp_request), ctypes.POINTER(i64)]),
+            "gp_server_wait": (ctypes.c_int, [P, i64, ctypes.POINTER(gp_response)]),
+            "gp_server_destroy": (None, [P]),
             "gp_modularity": (ctypes.c_int, [P, ctypes.POINTER(gp_graph), P, i32, ctypes.POINTER(gp_modularity_stats)]),
         }
         for name, (res, args) in sig.items():
@@ -482,3 +498,56 @@ def version() -> str:
 def launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     return int(_load().gp_launch_count())
+
+
+class Server:
+    """The library's request loop (gp_server_*): requests from host arrays, answered by worker
+    threads with their own streams, admitted against a device-memory budget."""
+
+    def __init__(self, device: int = 0, workers: int = 8, hbm_budget: int = 96 << 30,
+                 cfg: gp_config | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device available: the partitioner runs on the GPU only")
+        self.lib = _load()
+        p = ctypes.c_void_p()
+        st = self.lib.gp_server_create(ctypes.byref(p), device, workers, hbm_budget,
+                                       ctypes.byref(cfg) if cfg is not None else None)
+        if st != GP_OK:
+            raise GpError(st, "gp_server_create failed")
+        self.ptr = p.value
+        self._live = {}
+
+    def submit(self, g, k: int, eps: float, seed: int) -> int:
+        """g: a host graph (numpy CSR with int32 ids and weights).  Returns a ticket."""
+        arrs = [np.ascontiguousarray(g.xadj, dtype=np.int32), np.ascontiguousarray(g.adjncy, dtype=np.int32),
+                np.ascontiguousarray(g.vwgt, dtype=np.int32), np.ascontiguousarray(g.adjwgt, dtype=np.int32)]
+        blocks = np.empty(max(g.n, 1), dtype=np.int32)
+        r = gp_request(g.n, int(arrs[0][-1]) if g.n else 0, *[a.ctypes.data for a in arrs], k, eps, seed,
+                       blocks.ctypes.data)
+        t = ctypes.c_int64(0)
+        st = self.lib.gp_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(t))
+        if st != GP_OK:
+            raise GpError(st, "gp_server_submit failed")
+        self._live[t.value] = (arrs, blocks, g.n)
+        return t.value
+
+    def wait(self, ticket: int):
+        """Blocks until done.  Returns (blocks, cut, gp_response)."""
+        resp = gp_response()
+        st = self.lib.gp_server_wait(self.ptr, ticket, ctypes.byref(resp))
+        if st != GP_OK:
+            raise GpError(st, "gp_server_wait failed")
+        _, blocks, n = self._live.pop(ticket)
+        return blocks[:n], resp.cut, resp
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            self.lib.gp_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
