@@ -59,6 +59,18 @@ def workload_of(args):
     return SMALL if args.small else WORKLOAD
 
 
+def max_over_ranks(values):
+    """Element-wise maximum over all ranks (the slowest rank's times); a no-op on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,10 +340,7 @@ def run_gpu(args, world, rank, local):
         mod["what"] = ("Q_C, alpha_C and Lemma 2's bound 1 - Q_C - alpha_C for the level-1 clustering; "
                        "kept_edge_fraction = coarse edges / input edges before sparsification")
     coarsen_ms = sum(s[0] for s in stats)
-    if world > 1:
-        t = torch.tensor([step_ms, coarsen_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, coarsen_ms = float(t[0]), float(t[1])
+    step_ms, coarsen_ms = max_over_ranks([step_ms, coarsen_ms])
     value = world * g.m * args.steps / (coarsen_ms / 1000.0)
 
     # roofline of the dominant kernel class of the coarsening phase (by device time in the
@@ -380,10 +389,7 @@ def run_gpu(args, world, rank, local):
             ctx.gp_partition_host(n, m2, hx, ha, hv, hw, w["k"], w["eps"], w["seed"], blocks=hb)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t
-        if world > 1:
-            tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt[0])
+        e2e_s = max_over_ranks([e2e_s])[0]
         e2e = {"value": world * g.m * args.steps / e2e_s, "unit": "edges/s",
                "what": "gp_partition_host: H2D of the CSR, full partition, D2H of the block ids",
                "ms_per_step": 1000 * e2e_s / args.steps,

@@ -331,7 +331,7 @@ gp_status gp_server_create(gp_server **out, int device, int32_t workers, int64_t
                            const gp_config *cfg);
 /* Queues a request; *ticket identifies it for gp_server_wait. */
 gp_status gp_server_submit(gp_server *srv, const gp_request *req, int64_t *ticket);
-/* Blocks until the request is done, fills *out and forgets the ticket. */
+/* Blocks until the request is done, fills *out and forgets the ticket (wait once per ticket). */
 gp_status gp_server_wait(gp_server *srv, int64_t ticket, gp_response *out);
 /* Finishes the queued and running requests, then stops the workers. */
 void gp_server_destroy(gp_server *srv);

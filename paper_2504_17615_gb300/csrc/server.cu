@@ -158,16 +158,23 @@ gp_status gp_server_submit(gp_server *s, const gp_request *req, int64_t *ticket)
 gp_status gp_server_wait(gp_server *s, int64_t ticket, gp_response *out) {
   if (!s || !out) return GP_ERR_INVALID;
   std::unique_lock<std::mutex> lk(s->mu);
+  if (s->jobs.find(ticket) == s->jobs.end()) return GP_ERR_INVALID;
+  // a ticket is waited for once; a second waiter finds it gone and returns GP_ERR_INVALID
+  s->cv_done.wait(lk, [&] {
+    auto it = s->jobs.find(ticket);
+    return it == s->jobs.end() || it->second.done;
+  });
   auto it = s->jobs.find(ticket);
   if (it == s->jobs.end()) return GP_ERR_INVALID;
-  s->cv_done.wait(lk, [&] { return s->jobs[ticket].done; });
-  const Job &j = s->jobs[ticket];
+  const Job &j = it->second;
   out->status = j.status;
   out->cut = j.cut;
   out->queued_ms = ms(j.t_submit, j.t_start);
   out->run_ms = ms(j.t_start, j.t_end);
   out->total_ms = ms(j.t_submit, j.t_end);
-  s->jobs.erase(ticket);
+  s->jobs.erase(it);
+  lk.unlock();
+  s->cv_done.notify_all();
   return GP_OK;
 }
 
