@@ -58,6 +58,8 @@ def test_binding_fails_loudly_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         gp.Context(0)
+    with pytest.raises(RuntimeError):
+        gp.Server(0, workers=2)
 
 
 def test_no_cpu_fallback_in_the_package():
