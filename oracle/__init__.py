@@ -109,6 +109,7 @@ def _load():
                 "or_cluster_bound": (i64, [i64, i32, i32]),
                 "or_cluster": (ctypes.c_int, G + [i64, i32, u64, P, P, P, P]),
                 "or_coarsen": (ctypes.c_int, G + [i64, i32, u64, P, P, P, P]),
+                "or_coarsen_traced": (ctypes.c_int, G + [i64, i32, u64, P, P, P, P, P, P, i32]),
                 "or_contract": (ctypes.c_int, G + [P, i32, P, P, P, P]),
                 "or_sparsify": (ctypes.c_int, G + [i64, i32, u64, i32, P, P, P, P, P]),
                 "or_m_hat": (i64, [i64, i64, i64, P]),
@@ -211,6 +212,36 @@ def coarsen(g, U: int, level: int, seed: int, cfg: Config | None = None):
     if rc != OK:
         raise RuntimeError(f"or_coarsen failed: {rc}")
     return cmap, nc.value, st
+
+
+def coarsen_traced(g, U: int, level: int, seed: int, cfg: Config | None = None, max_digests: int = 512):
+    """or_coarsen plus the cluster labels and the label digest after every LP sub-round:
+    (label, cmap, n_coarse, Level, digests)."""
+    cfg = cfg or Config.default()
+    keep, a = _args(g)
+    label = np.empty(g.n, dtype=np.int32)
+    cmap = np.empty(g.n, dtype=np.int32)
+    nc = ctypes.c_int32(0)
+    st = Level()
+    dig = np.zeros(max_digests, dtype=np.uint64)
+    rc = _load().or_coarsen_traced(*a, U, level, seed, ctypes.byref(cfg), label.ctypes.data,
+                                   cmap.ctypes.data, ctypes.byref(nc), ctypes.byref(st),
+                                   dig.ctypes.data, max_digests)
+    if rc != OK:
+        raise RuntimeError(f"or_coarsen_traced failed: {rc}")
+    return label, cmap, nc.value, st, dig[:min(st.lp_subrounds, max_digests)]
+
+
+def label_digest(label) -> int:
+    """The digest or_coarsen_traced records: sum of mix(v << 32 | label[v]) mod 2^64."""
+    lab = np.asarray(label, dtype=np.int64) & 0xFFFFFFFF
+    v = np.arange(len(lab), dtype=np.uint64)
+    z = (v << np.uint64(32)) | lab.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+        return int(z.sum(dtype=np.uint64))
 
 
 def _take_graph(n, px, pa, pv, pw) -> HostGraph:

@@ -144,6 +144,11 @@ typedef struct {
   int32_t v;
 } prop_t;
 
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x > y) - (x < y);
+}
+
 static int prop_cmp(const void *a, const void *b) {
   const prop_t *x = (const prop_t *)a, *y = (const prop_t *)b;
   if (x->k != y->k) return x->k < y->k ? -1 : 1;
@@ -158,7 +163,18 @@ typedef struct {
   int count_clusters; /* clustering: track non-empty clusters and stop at n_min */
   int64_t n_min;
   int32_t dbg_max_subrounds;
+  uint64_t *digests;   /* optional: label digest after each sub-round (tests) */
+  int32_t max_digests;
 } lp_params;
+
+/* Digest of a labelling: sum over v of mix(v << 32 | label[v]), modulo 2^64.
+ * Equal labellings give equal digests; any difference changes the digest
+ * unless a 2^-64 coincidence.  Test instrumentation only. */
+static uint64_t label_digest(int32_t n, const int32_t *label) {
+  uint64_t d = 0;
+  for (int32_t v = 0; v < n; v++) d += mix(((uint64_t)(uint32_t)v << 32) | (uint32_t)label[v]);
+  return d;
+}
 
 /*
  * Size-constrained label propagation (Sec. 3, KaMinPar's LP; Sec. 4.1).
@@ -173,7 +189,18 @@ typedef struct {
  * by (h32(key(PRIO), v, 0), v) are accepted while the snapshot weight plus
  * the accepted weight stays within the bound (longest prefix, R7).  Stops
  * after a round without moves (R3) and, when clustering, as soon as the
- * number of non-empty clusters reaches n_min (R8, the 2.5x cap of Sec. 4.3).
+ * number of non-empty clusters reaches n_min.
+ *
+ * The node reduction of a level is at most 2.5x (Sec. 4.3), so the clustering
+ * never goes below n_min clusters (R8): with c clusters at the start of a
+ * sub-round, at most D = c - n_min of them may be emptied by its moves.  All
+ * accepted moves carry the key (h32(key(PRIO), v, 0), v).  A cluster all of
+ * whose members leave in the sub-round is emptied at the largest key among its
+ * departures (arrivals are not counted, so a refilled cluster still counts as
+ * emptied).  If more than D clusters are emptied, only the moves whose key is
+ * below the (D+1)-th smallest emptying key are applied: the D clusters emptied
+ * first lose all their members, every other cluster keeps at least one, and
+ * at least n_min clusters remain.
  */
 static void lp_run(const og *g, int32_t *label, int64_t *weight, int64_t nlabels, uint64_t seed,
                    const lp_params *P, int64_t *nclusters, int32_t *subrounds_run,
@@ -184,9 +211,14 @@ static void lp_run(const og *g, int32_t *label, int64_t *weight, int64_t nlabels
   prop_t *props = (prop_t *)malloc(sizeof(prop_t) * ((size_t)n + 1));
   char *accept = (char *)malloc((size_t)n + 1);
   int32_t *size = NULL;
+  int64_t *dep_w = NULL;  /* R8: weight leaving each cluster in the sub-round */
+  uint64_t *dep_key = NULL, *empt = NULL;  /* R8: latest departure key; emptying keys */
   if (P->count_clusters) {
     size = (int32_t *)calloc((size_t)nlabels + 1, sizeof(int32_t));
     for (int32_t v = 0; v < n; v++) size[label[v]]++;
+    dep_w = (int64_t *)calloc((size_t)nlabels + 1, sizeof(int64_t));
+    dep_key = (uint64_t *)calloc((size_t)nlabels + 1, sizeof(uint64_t));
+    empt = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)n + 1));
   }
   int32_t sub_done = 0;
   int64_t total_moves = 0;
@@ -248,7 +280,39 @@ static void lp_run(const og *g, int32_t *label, int64_t *weight, int64_t nlabels
         }
         i = j;
       }
-      /* 3. apply */
+      /* 3. the 2.5x cap (R8): at most D = c - n_min clusters may be emptied */
+      if (P->count_clusters) {
+        int64_t D = *nclusters - P->n_min;
+        for (int64_t t = 0; t < np; t++) {
+          if (!accept[t]) continue;
+          int32_t own = label[props[t].v];
+          uint64_t kv = ((uint64_t)props[t].prio << 32) | (uint32_t)props[t].v;
+          dep_w[own] += g->vwgt[props[t].v];
+          if (kv > dep_key[own]) dep_key[own] = kv;
+        }
+        int64_t E = 0;
+        for (int64_t t = 0; t < np; t++) {
+          if (!accept[t]) continue;
+          int32_t own = label[props[t].v];
+          uint64_t kv = ((uint64_t)props[t].prio << 32) | (uint32_t)props[t].v;
+          /* a cluster is emptied iff all of its weight leaves; count it once, at its latest key */
+          if (dep_w[own] == weight[own] && kv == dep_key[own]) empt[E++] = kv;
+        }
+        if (E > D) {
+          qsort(empt, (size_t)E, sizeof(uint64_t), cmp_u64);
+          uint64_t cutoff = empt[D];
+          for (int64_t t = 0; t < np; t++) {
+            uint64_t kv = ((uint64_t)props[t].prio << 32) | (uint32_t)props[t].v;
+            if (accept[t] && kv >= cutoff) accept[t] = 0;
+          }
+        }
+        for (int64_t t = 0; t < np; t++) {
+          int32_t own = label[props[t].v];
+          dep_w[own] = 0;
+          dep_key[own] = 0;
+        }
+      }
+      /* 4. apply */
       int64_t moved = 0;
       for (int64_t t = 0; t < np; t++) {
         if (!accept[t]) continue;
@@ -265,6 +329,7 @@ static void lp_run(const og *g, int32_t *label, int64_t *weight, int64_t nlabels
         *nclusters = cnt;
       }
       round_moves += moved;
+      if (P->digests && sub_done < P->max_digests) P->digests[sub_done] = label_digest(n, label);
       sub_done++;
     }
     total_moves += round_moves;
@@ -273,6 +338,7 @@ static void lp_run(const og *g, int32_t *label, int64_t *weight, int64_t nlabels
   if (subrounds_run) *subrounds_run = sub_done;
   if (moves_out) *moves_out = total_moves;
   free(rating); free(touched); free(props); free(accept); free(size);
+  free(dep_w); free(dep_key); free(empt);
 }
 
 /* ------------------------------------------------------------ clustering */
@@ -300,6 +366,10 @@ static int fav_cmp(const void *a, const void *b) {
  * Isolated nodes (R10): light degree-0 nodes in id order, runs of g =
  * floor(U / heaviest light isolated node), same stop rule.
  */
+/* set only for the duration of or_coarsen_traced (single-threaded use per call) */
+static __thread uint64_t *g_digests = NULL;
+static __thread int32_t g_max_digests = 0;
+
 int or_cluster(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
                const int32_t *adjwgt, int64_t U, int32_t level, uint64_t seed,
                const or_config *cfg, int32_t *label, int64_t *nclusters_out, or_level *st) {
@@ -315,6 +385,7 @@ int or_cluster(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int3
   P.level = level; P.rounds = cfg->lp_rounds; P.subrounds = cfg->lp_subrounds;
   P.bound = U; P.count_clusters = 1; P.n_min = n_min;
   P.dbg_max_subrounds = cfg->dbg_max_subrounds;
+  P.digests = g_digests; P.max_digests = g_max_digests;
   int32_t subs = 0;
   int64_t moves = 0;
   lp_run(&g, label, cw, n, seed, &P, &nclusters, &subs, &moves);
@@ -421,6 +492,23 @@ int or_coarsen(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int3
   int rc = or_cluster(n, xadj, adjncy, vwgt, adjwgt, U, level, seed, cfg, label, NULL, st);
   if (rc == OR_OK) *n_coarse = relabel(n, label, cmap);
   free(label);
+  return rc;
+}
+
+/*
+ * or_coarsen plus the labels (cluster ids before relabelling) and, for tests,
+ * the label digest after every clustering LP sub-round (at most max_digests).
+ */
+int or_coarsen_traced(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                      const int32_t *adjwgt, int64_t U, int32_t level, uint64_t seed,
+                      const or_config *cfg, int32_t *label, int32_t *cmap, int32_t *n_coarse,
+                      or_level *st, uint64_t *digests, int32_t max_digests) {
+  g_digests = digests;
+  g_max_digests = max_digests;
+  int rc = or_cluster(n, xadj, adjncy, vwgt, adjwgt, U, level, seed, cfg, label, NULL, st);
+  g_digests = NULL;
+  g_max_digests = 0;
+  if (rc == OR_OK) *n_coarse = relabel(n, label, cmap);
   return rc;
 }
 
@@ -821,6 +909,7 @@ int or_refine(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32
   P.level = level; P.rounds = cfg->ref_rounds; P.subrounds = cfg->lp_subrounds;
   P.bound = Lmax; P.count_clusters = 0; P.n_min = 0;
   P.dbg_max_subrounds = -1;
+  P.digests = NULL; P.max_digests = 0;
   int64_t moves = 0;
   lp_run(&g, blk, bw, k, seed, &P, NULL, NULL, &moves);
   if (moves_out) *moves_out = moves;

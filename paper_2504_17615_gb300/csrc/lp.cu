@@ -836,7 +836,13 @@ struct ApplyArgs {
   uint8_t *label8;
   int nshared;       // > 0: few labels; weight changes summed per block in shared memory
   Counters *cnt;
+  const uint64_t *cutoff;  // 2.5x cap: only moves with key (h32(PRIO), v) below *cutoff apply (null: all)
+  uint64_t kprio;
 };
+
+__device__ __forceinline__ uint64_t move_key(uint64_t kprio, int v) {
+  return ((uint64_t)h32(kprio, (uint32_t)v, 0) << 32) | (uint32_t)v;
+}
 
 __device__ __forceinline__ void proposal(const ApplyArgs &a, int t, int &v, int &K, int &own, int &c,
                                          bool &mv) {
@@ -862,6 +868,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
     int v, K, own, c;
     bool mv;
     proposal(a, t, v, K, own, c, mv);
+    if (mv && a.cutoff && move_key(a.kprio, v) >= *a.cutoff) mv = false;
     if (mv) {
       a.label[v] = K;
       if (a.label8) a.label8[v] = (uint8_t)K;
@@ -883,6 +890,67 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
   moved = warp_sum(moved);
   if (lane_id() == 0 && moved)
     atomicAdd((unsigned long long *)&a.cnt->moved_sub, (unsigned long long)moved);
+}
+
+// ------------------------------------------------------- the 2.5x cap
+//
+// The node reduction of a clustering is at most 2.5x (Sec. 4.3): with c
+// clusters at the start of a sub-round, its moves may empty at most D =
+// c - n_min of them.  A cluster all of whose weight leaves is emptied at the
+// largest move key (h32(PRIO), node) among its departures (arrivals are not
+// counted); if more than D clusters are emptied, only the moves below the
+// (D+1)-th smallest emptying key apply.  These kernels run before k_apply, on
+// the snapshot labels and weights, and only in sub-rounds whose accepted moves
+// could exceed D.
+
+// Departure weight and latest departure key per source cluster.
+__global__ void __launch_bounds__(kThreads) k_cap_depart(ApplyArgs a, int32_t *depw,
+                                                         unsigned long long *dkey) {
+  const int total = a.nmov + a.nov;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int v, K, own, c;
+    bool mv;
+    proposal(a, t, v, K, own, c, mv);
+    if (!mv) continue;
+    atomicAdd(&depw[own], c);
+    atomicMax(&dkey[own], (unsigned long long)move_key(a.kprio, v));
+  }
+}
+
+// The emptying key of every emptied cluster (listed once, by its latest mover);
+// then clears the per-cluster state of the sources.
+__global__ void __launch_bounds__(kThreads) k_cap_collect(ApplyArgs a, const int32_t *depw,
+                                                          const unsigned long long *dkey,
+                                                          uint64_t *ekeys, int *ecount) {
+  const int total = a.nmov + a.nov;
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const int t = base + (int)threadIdx.x;
+    bool emit_key = false;
+    uint64_t key = 0;
+    if (t < total) {
+      int v, K, own, c;
+      bool mv;
+      proposal(a, t, v, K, own, c, mv);
+      if (mv) {
+        key = move_key(a.kprio, v);
+        emit_key = depw[own] == a.weight[own] && key == dkey[own];
+      }
+    }
+    const int pos = warp_append(ecount, emit_key);
+    if (emit_key) ekeys[pos] = key;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cap_clear(ApplyArgs a, int32_t *depw, unsigned long long *dkey) {
+  const int total = a.nmov + a.nov;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int v, K, own, c;
+    bool mv;
+    proposal(a, t, v, K, own, c, mv);
+    if (!mv) continue;
+    depw[own] = 0;
+    dkey[own] = 0;
+  }
 }
 
 // Closes a sub-round in one launch: clears the incoming weights of its
@@ -1092,6 +1160,11 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   }
   DBuf<Counters> counters(ctx, 1);
   Counters *C = counters.get();
+  // the 2.5x cap (clustering): departure weight and latest key per cluster, emptying keys
+  DBuf<int32_t> cap_w;
+  DBuf<unsigned long long> cap_k;
+  DBuf<uint64_t> cap_e;
+  DBuf<int> cap_n;
   DBuf<unsigned> done(ctx, 1);
   done.zero();
   incoming.zero();
@@ -1154,12 +1227,12 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
                                                       ov_key.get(), ov_val.get(), C, kprio);
         GP_LAUNCH_CHECK();
       }
-      int hdr[3];
+      Counters hdr;
       const auto t_sync0 = std::chrono::steady_clock::now();
-      read_back(ctx, C, sizeof(hdr), hdr);
+      read_back(ctx, C, sizeof(hdr), &hdr);
       sync_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_sync0).count();
-      if (hdr[0]) { stop = true; break; }
-      const int nov = hdr[1], nmov = hdr[2];
+      if (hdr.stop) { stop = true; break; }
+      const int nov = hdr.nov, nmov = hdr.nmov;
       subs++;
       res.overflow_total += nov;
       if (nov > res.overflow_max) res.overflow_max = nov;
@@ -1212,7 +1285,34 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         aa.ov_acc = ov_acc.get(); aa.nmov = nmov; aa.nov = nov; aa.vwgt = g.vwgt; aa.label = label;
         aa.weight = weight; aa.incoming = incoming.get(); aa.label8 = label8;
         aa.nshared = agg ? (int)nlabels : 0; aa.cnt = C;
+        aa.kprio = kprio;
         const int ga = grid_for((int64_t)nmov + nov, kThreads, grid);
+        // the 2.5x cap: only when the accepted moves could empty more than D clusters
+        const int64_t D = hdr.nclusters - p.n_min;
+        if (p.count_clusters && (int64_t)nmov + nov > D) {
+          if (!cap_w.get()) {
+            cap_w.reset(ctx, (size_t)nlabels);
+            cap_k.reset(ctx, (size_t)nlabels);
+            cap_w.zero();
+            cap_k.zero();
+            cap_e.reset(ctx, (size_t)n);
+            cap_n.reset(ctx, 1);
+          }
+          cap_n.zero();
+          k_cap_depart<<<ga, kThreads, 0, ctx->stream>>>(aa, cap_w.get(), cap_k.get());
+          GP_LAUNCH_CHECK();
+          k_cap_collect<<<ga, kThreads, 0, ctx->stream>>>(aa, cap_w.get(), cap_k.get(), cap_e.get(), cap_n.get());
+          GP_LAUNCH_CHECK();
+          k_cap_clear<<<ga, kThreads, 0, ctx->stream>>>(aa, cap_w.get(), cap_k.get());
+          GP_LAUNCH_CHECK();
+          const int E = read_scalar(ctx, cap_n.get());
+          if (E > D) {
+            DBuf<uint32_t> dummy(ctx, (size_t)E);
+            radix_sort_pairs(ctx, cap_e.get(), dummy.get(), E, 64);
+            aa.cutoff = cap_e.get() + D;
+            res.capped++;
+          }
+        }
         if (nmov + nov > 0) {
           k_apply<<<ga, kThreads, sizeof(int) * aa.nshared, ctx->stream>>>(aa);
           GP_LAUNCH_CHECK();
@@ -1235,10 +1335,10 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
     const double host_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_host0).count();
     fprintf(stderr,
             "[gp lp] %s level=%d n=%d m2=%lld labels=%lld subrounds=%d moves=%lld proposals=%lld "
-            "overflow_total=%lld overflow_max=%lld host_ms=%.2f sync_ms=%.2f ms=%.2f\n",
+            "overflow_total=%lld overflow_max=%lld capped=%d host_ms=%.2f sync_ms=%.2f ms=%.2f\n",
             p.count_clusters ? "cluster" : "refine", p.level, n, (long long)g.m2, (long long)nlabels, subs,
             (long long)res.moves, (long long)res.proposals, (long long)res.overflow_total,
-            (long long)res.overflow_max, 1000 * host_s, 1000 * sync_s, trace.ms());
+            (long long)res.overflow_max, res.capped, 1000 * host_s, 1000 * sync_s, trace.ms());
   }
   if (p.count_clusters && nclusters_dev)
     GP_CUDA(cudaMemcpyAsync(nclusters_dev, &C->nclusters, sizeof(int64_t), cudaMemcpyDeviceToDevice,

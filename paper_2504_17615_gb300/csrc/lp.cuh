@@ -35,6 +35,7 @@ struct LpResult {
   int64_t proposals = 0;       // over all sub-rounds
   int64_t overflow_total = 0;  // proposers of overflowing targets, over all sub-rounds
   int64_t overflow_max = 0;    // largest such set in one sub-round
+  int32_t capped = 0;          // sub-rounds cut short by the 2.5x cap
 };
 
 // Runs LP on g.  label (n) and weight (nlabels) are updated in place; size

@@ -397,3 +397,52 @@ def test_modularity_rejects_labels_out_of_range(gp, ctx):
     lab[17] = 5
     with pytest.raises(gp.GpError):
         ctx.gp_modularity(dg, lab, 5)
+
+
+# ------------------------------------------------- hand-traced schedule pins
+
+from tests.test_schedule_pins import CASES as PIN_CASES, config_of, graph_of, ints  # noqa: E402
+
+
+@pytest.mark.parametrize("c", PIN_CASES, ids=[c["case"] for c in PIN_CASES])
+def test_schedule_pins_on_gpu(gp, ctx, c):
+    """The GPU reaches the hand-traced results of the schedule readings (R6, R7, R8,
+    R18, R19) through the C-ABI, and agrees with the oracle on them."""
+    import torch
+    g = graph_of(c)
+    kw = {k: getattr(config_of(c), k) for k in ("lp_rounds", "lp_subrounds", "ref_rounds", "ip_trials",
+                                                 "two_hop", "isolated", "dbg_max_subrounds")}
+    if "trials" in c:
+        kw["ip_trials"] = int(c["trials"])
+    cfg = gp.default_config(**kw)
+    dg = gp.DeviceGraph.from_host(g)
+    call = c["call"]
+    if call == "cluster":
+        _, nc, st, label = ctx.gp_coarsen(dg, int(c["U"]), int(c["level"]), int(c["seed"]), cfg,
+                                          want_label=True)
+        label = label.cpu().numpy()
+        if "expect_label" in c:
+            assert label.tolist() == ints(c["expect_label"])
+        for tok in c.get("expect_label_at", "").split():
+            v, _, lab = tok.partition(":")
+            assert int(label[int(v)]) == int(lab), tok
+        if "expect_nclusters" in c:
+            assert nc == int(c["expect_nclusters"])
+        if "expect_subrounds" in c:
+            assert st.lp_subrounds == int(c["expect_subrounds"])
+        assert st.lp_moves == int(c["expect_moves"])
+    elif call in ("refine", "rebalance"):
+        blk = torch.tensor(ints(c["blocks"]), dtype=torch.int32, device="cuda")
+        if call == "refine":
+            mv = ctx.gp_refine(dg, int(c["k"]), int(c["Lmax"]), int(c["level"]), int(c["seed"]), blk, cfg)
+        else:
+            mv = ctx.gp_rebalance(dg, int(c["k"]), int(c["Lmax"]), blk)
+        assert blk.cpu().numpy().tolist() == ints(c["expect_blocks"])
+        assert mv == int(c["expect_moves"])
+    elif call == "initial_partition":
+        blk = ctx.gp_initial_partition(dg, int(c["k"]), int(c["eps_ppm"]) / 1e6, int(c["seed"]), cfg)
+        side = set(ints(c["expect_block0"]))
+        want = np.array([0 if v in side else 1 for v in range(g.n)], dtype=np.int32)
+        assert np.array_equal(blk.cpu().numpy(), want)
+    else:
+        raise AssertionError(call)

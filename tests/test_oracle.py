@@ -267,8 +267,24 @@ def test_cluster_bound_and_cap_invariants():
         heavy = g.vwgt > U
         assert (w[label[~heavy]] <= U).all()
         assert len(np.unique(label)) == ncl
-        # stops at n_min at the latest one sub-round after crossing it
-        assert ncl >= n_min - g.n // orc.Config.default().lp_subrounds
+        # Sec. 4.3: at most a 2.5x node reduction, exactly
+        assert ncl >= n_min
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_lp_cap_is_exact_when_lp_would_overshoot(seed):
+    # a random graph with a generous U shrinks well past 2.5x without the cap; with it
+    # the level ends at n_min clusters (plus the clusters a refill keeps alive)
+    g = gg.er(6000, 30000, seed)
+    n_min = math.ceil(2 * g.n / 5)
+    for S in (1, 2, 8):
+        cfg = orc.Config.default(lp_subrounds=S, two_hop=0, isolated=0)
+        label, ncl, st = orc.cluster(g, 50, 1, seed, cfg)
+        assert ncl >= n_min
+        assert ncl <= n_min + g.n // 100, (S, ncl, n_min)
+        assert len(np.unique(label)) == ncl
+        cmap, nc, _ = orc.coarsen(g, 50, 1, seed, cfg)
+        assert 5 * nc >= 2 * g.n  # n / n' <= 2.5
 
 
 def test_coarsen_gives_dense_ids():
