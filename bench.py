@@ -41,7 +41,7 @@ CPU_SAMPLE = dict(name="erdos_renyi_n2^21_m20971520_k128", n=1 << 21, m=20_971_5
 FALLBACK_HBM_GBS = 6800.0
 # profile classes of the coarsening phase (the rest belong to initial partitioning and uncoarsening,
 # or are shared: sort, scan, round_setup)
-COARSEN_CLASSES = ("lp_rate", "lp_accept", "lp_overflow", "lp_apply", "two_hop", "relabel", "contract",
+COARSEN_CLASSES = ("lp_rate", "lp_accept", "lp_overflow", "lp_apply", "lp_small", "two_hop", "relabel", "contract",
                    "contract_aux", "sparsify")
 # ncu DRAM traffic per algorithmic byte, by class, with the sources the counters were taken on
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")

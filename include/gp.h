@@ -89,6 +89,8 @@ typedef struct gp_config {
   int32_t max_levels;                 /* cap on the hierarchy depth (<= 64) */
   int32_t dbg_max_subrounds;          /* < 0: no limit; else stop clustering LP early (tests) */
   int32_t validate;                   /* gp_partition: 1 = full input validation */
+  int32_t small_lp_nodes;             /* LP runs on graphs of at most this many nodes use one
+                                         persistent launch (0: never); same results either way */
 } gp_config;
 
 /* Per-level record of one coarsening step (Alg. 1 quantities). */
@@ -123,6 +125,16 @@ void gp_config_default(gp_config *cfg);
  */
 gp_status gp_create(gp_ctx **ctx, int device, void *stream, const gp_allocator *alloc);
 void gp_destroy(gp_ctx *ctx);
+/*
+ * Upper bound on the iterations of every grid-wide wait inside the library's
+ * persistent kernels (the small-graph label propagation).  A wait that runs
+ * out makes the call return GP_ERR_TIMEOUT; the context stays usable and the
+ * call's outputs are undefined.  spins = 0 restores the default (several
+ * seconds of waiting); spins < 0 makes every wait give up at once (tests).
+ * Not an algorithm parameter: no counterpart in the paper.
+ */
+void gp_set_wait_limit(gp_ctx *ctx, int64_t spins);
+
 /* Text of the last error on this context ("" if none).  Owned by ctx. */
 const char *gp_last_error(const gp_ctx *ctx);
 /* Library build string (version, compute capability compiled for). */

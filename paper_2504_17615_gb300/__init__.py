@@ -68,7 +68,7 @@ _CFG_FIELDS = ("tau_e_num", "tau_e_den", "tau_d_num", "tau_d_den", "rho_num", "r
                "cluster_factor", "coarsest_factor", "shrink_num", "shrink_den",
                "min_shrink_num", "min_shrink_den", "lp_rounds", "lp_subrounds", "ref_rounds",
                "ip_trials", "sparsifier", "two_hop", "isolated", "max_levels",
-               "dbg_max_subrounds", "validate")
+               "dbg_max_subrounds", "validate", "small_lp_nodes")
 
 
 class gp_config(ctypes.Structure):
@@ -134,6 +134,7 @@ def _load():
             "gp_launch_count": (i64, []),
             "gp_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P, ctypes.POINTER(gp_allocator)]),
             "gp_destroy": (None, [P]),
+            "gp_set_wait_limit": (None, [P, i64]),
             "gp_last_error": (ctypes.c_char_p, [P]),
             "gp_coarsen": (ctypes.c_int, [P, G, i64, i32, u64, C, P, P, ctypes.POINTER(i32), S]),
             "gp_contract": (ctypes.c_int, [P, G, P, i32, G]),
@@ -339,6 +340,10 @@ class Context:
             raise GpError(st, (self.lib.gp_last_error(self.ptr) or b"").decode())
 
     # --- the C-ABI calls, same names ---
+
+    def gp_set_wait_limit(self, spins: int):
+        """Iteration limit of device-side waits (0: default, < 0: give up at once)."""
+        self.lib.gp_set_wait_limit(self.ptr, int(spins))
 
     def gp_coarsen(self, g, U: int, level: int, seed: int, cfg: gp_config | None = None,
                    want_label: bool = False):

@@ -1,6 +1,6 @@
 // api.cu -- the C-ABI of include/gp.h: argument checks, error capture and
 // the context.  No exception crosses this boundary.
-#include "gp_internal.cuh"
+#include "lp.cuh"
 
 namespace {
 
@@ -46,7 +46,7 @@ const char *kProfNames[gp::PROF_COUNT_] = {
     "lp_rate",  "lp_accept", "refine_rate", "refine_accept", "round_setup", "two_hop",
     "relabel",  "contract",  "contract_aux", "sparsify",     "initial",     "project",
     "cut",      "validate",  "sort",         "scan",          "lp_overflow", "lp_apply",
-    "refine_overflow", "refine_apply", "rebalance"};
+    "refine_overflow", "refine_apply", "rebalance", "lp_small", "refine_small"};
 
 }  // namespace
 
@@ -70,6 +70,11 @@ void gp_config_default(gp_config *c) {
   c->max_levels = GP_MAX_LEVELS;
   c->dbg_max_subrounds = -1;
   c->validate = 1;
+  c->small_lp_nodes = gp::kLpSmallMaxNodes;
+}
+
+void gp_set_wait_limit(gp_ctx *ctx, int64_t spins) {
+  if (ctx) ctx->wait_spins = spins;
 }
 
 const char *gp_version(void) { return "gp-gb300 1.0 (sm_103a)"; }
@@ -125,7 +130,7 @@ void gp_destroy(gp_ctx *ctx) {
     cudaStreamDestroy(s);
   }
   ctx->workers.clear();
-  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
   for (auto &r : ctx->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -334,6 +339,8 @@ gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, dou
     switch (i) {
       case gp::PROF_LP_RATE:
       case gp::PROF_REF_RATE:
+      case gp::PROF_LP_SMALL:
+      case gp::PROF_REF_SMALL:
         // per entry: neighbour id, edge weight, neighbour label (12 B, 9 B when the
         // labels are one byte); per candidate label its weight (4 B); per node
         // offsets, weight, own label (16 B); per proposal target write + incoming

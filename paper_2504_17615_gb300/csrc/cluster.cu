@@ -135,7 +135,8 @@ void coarsen_level(gp_ctx *ctx, const DevGraph &g, int64_t U, int32_t level, uin
   p.bound = U; p.count_clusters = true; p.n_min = n_min;
   p.dbg_max_subrounds = cfg.dbg_max_subrounds;
   p.prof_rate = PROF_LP_RATE; p.prof_accept = PROF_LP_ACCEPT;
-  p.prof_overflow = PROF_LP_OVERFLOW; p.prof_apply = PROF_LP_APPLY;
+  p.prof_overflow = PROF_LP_OVERFLOW; p.prof_apply = PROF_LP_APPLY; p.prof_small = PROF_LP_SMALL;
+  p.small_nodes = cfg.small_lp_nodes;
   LpResult r = lp_run(ctx, g, label, cw.get(), n, seed, p, ncl_dev.get());
   int64_t ncl = n == 0 ? 0 : r.nclusters;
   out.st.n = n;

@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gp.h"
 
 namespace gp {
@@ -72,6 +74,8 @@ enum ProfClass {
   PROF_REF_OVERFLOW,
   PROF_REF_APPLY,
   PROF_REBALANCE,     // greedy rebalance after the initial partition
+  PROF_LP_SMALL,      // clustering LP of a small graph in one persistent launch
+  PROF_REF_SMALL,     // refinement LP of a small graph in one persistent launch
   PROF_COUNT_
 };
 
@@ -108,6 +112,7 @@ struct gp_ctx {
   unsigned long long *d_units = nullptr;  // PROF_COUNT_ x PROF_UNITS
   double prof_host_bytes[gp::PROF_COUNT_] = {};  // algorithmic bytes of classes sized on the host
   std::vector<gp_ctx *> workers;                 // batch workers (own streams and pools)
+  int64_t wait_spins = 0;                        // limit of device-side waits (0: default)
 };
 
 namespace gp {
@@ -178,6 +183,20 @@ struct ProfScope {
   cudaEvent_t a = nullptr;
   ProfScope(gp_ctx *c, int k);
   ~ProfScope();
+};
+
+// A named NVTX range around a phase of the method (visible to profilers such
+// as ncu --nvtx; costs nothing without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  NvtxRange(const char *what, int level) {
+    char buf[48];
+    snprintf(buf, sizeof buf, "%s_L%d", what, level);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Wall time of a stretch of stream work, measured only when the GP_TRACE

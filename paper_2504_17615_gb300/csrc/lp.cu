@@ -44,6 +44,7 @@ struct RateArgs {
   int32_t *gkeys, *gvals;  // large kernel global tables
   int64_t gstride;
   unsigned long long *units;
+  int wlabels;          // labels whose weights a launch may copy to shared memory (<= 256)
 };
 
 __device__ __forceinline__ void add_units(unsigned long long *units, unsigned long long e,
@@ -90,7 +91,11 @@ __device__ __forceinline__ void emit(const RateArgs &a, int i, int v, int best, 
 // leading candidate's weight is fetched; if it does not fit, it is dropped
 // and the next one is tried.  This picks exactly the best admissible
 // candidate while reading one label weight per node in the usual case, and
-// none at all when no neighbouring label beats the node's own label.
+// none at all when no neighbouring label beats the node's own label.  With
+// one-byte labels (refinement: at most 255 labels) the label weights are
+// copied to shared memory once per launch and every candidate is checked
+// against the bound up front, so the first pass already picks the best
+// admissible label.
 
 // Label kinds: LK_WIDE int32 labels summed in hash tables; LK_NARROW uint8
 // labels (fewer than 256) in hash tables; LK_DENSE uint8 labels below
@@ -107,7 +112,13 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
   constexpr int TW = LK == LK_DENSE ? U * NV * kDenseLabels : U * 64;  // table words per warp
   __shared__ int s_tk[LK == LK_DENSE ? 1 : kWarpsPerBlock][LK == LK_DENSE ? 1 : U * 64];
   __shared__ int s_tv[kWarpsPerBlock][TW];
+  constexpr bool kSmemW = MODE == RATE_LP && LK != LK_WIDE;
+  __shared__ int s_w[kSmemW ? 256 : 1];
   if (a.stop && *a.stop) return;
+  if (kSmemW) {
+    for (int t = threadIdx.x; t < a.wlabels; t += blockDim.x) s_w[t] = a.weight[t];
+    __syncthreads();
+  }
   const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane % G;
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
@@ -204,8 +215,9 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
     for (int q = 0; q < U; q++) {
       alive[q] = lead[q] && L[q] != own[q];
       uc += alive[q];
+      if (kSmemW && alive[q]) alive[q] = (int64_t)s_w[L[q]] + cv[q] <= a.bound;
       searching[q] = v[q] >= 0;
-      eager[q] = false;
+      eager[q] = kSmemW;
       best[q] = 0xFFFFFFFFu;
     }
     for (int it = 0; it <= G; it++) {  // bounded: every pass drops one candidate per searching group
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
 #pragma unroll
       for (int q = 0; q < U; q++) any = any || searching[q];
       if (!__any_sync(FULL, any)) break;
-      if (MODE == RATE_LP) {
+      if (MODE == RATE_LP && !kSmemW) {
         int we[U];
 #pragma unroll
         for (int q = 0; q < U; q++) we[q] = (eager[q] && searching[q] && alive[q]) ? a.weight[L[q]] : 0;
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
         c[q] = __reduce_min_sync(gmask, (top && h == hmin) ? (unsigned)L[q] : 0xFFFFFFFFu);
         holder[q] = top && h == hmin && (unsigned)L[q] == c[q];
       }
-      if (MODE != RATE_LP) {
+      if (MODE != RATE_LP || kSmemW) {
 #pragma unroll
         for (int q = 0; q < U; q++)
           if (searching[q]) { best[q] = c[q]; searching[q] = false; }
@@ -1128,6 +1140,7 @@ int bits_for(int64_t x) {
 
 LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int64_t nlabels, uint64_t seed, const LpParams &p, int64_t *nclusters_dev,
                 uint8_t *label8) {
+  if (lp_small_applicable(g, p)) return lp_run_small(ctx, g, label, weight, nlabels, seed, p, nclusters_dev, label8);
   LpResult res;
   const int n = g.n;
   const int S = p.subrounds;
@@ -1212,6 +1225,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       a.label = label; a.weight = weight; a.list = list.get(); a.offs = offs.get();
       a.bound = p.bound; a.ktie = ktie; a.prop = prop.get(); a.incoming = incoming.get();
       a.stop = &C->stop; a.units = units_rate; a.label8 = label8;
+      a.wlabels = label8 ? (int)nlabels : 0;
       {
         ProfScope ps(ctx, p.prof_rate);
         int hcnt[kNumBuckets];

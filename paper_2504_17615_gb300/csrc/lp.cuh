@@ -18,6 +18,13 @@ __host__ __device__ __forceinline__ int degree_bucket(int deg) {
 
 enum RateMode { RATE_LP = 0, RATE_FAV = 1 };
 
+// LP runs on graphs up to this size use the persistent kernel of lp_small.cu
+// (gp_config.small_lp_nodes, default) and at most this many CSR entries.
+constexpr int32_t kLpSmallMaxNodes = 1 << 20;
+constexpr int64_t kLpSmallMaxEntries = (int64_t)1 << 26;
+// iterations of a device-side wait before it gives up (about seconds)
+constexpr long long kDefaultWaitSpins = 1ll << 25;
+
 struct LpParams {
   uint32_t tag_act, tag_tie, tag_prio;
   int32_t level, rounds, subrounds;
@@ -25,7 +32,8 @@ struct LpParams {
   bool count_clusters;
   int64_t n_min;
   int32_t dbg_max_subrounds;
-  int prof_rate, prof_accept, prof_overflow, prof_apply;
+  int32_t small_nodes;  // graphs up to this many nodes: one persistent launch (0: never)
+  int prof_rate, prof_accept, prof_overflow, prof_apply, prof_small;
 };
 
 struct LpResult {
@@ -56,5 +64,11 @@ void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, c
                          int64_t U, uint64_t kfav, DBuf<uint64_t> &keys, int32_t &count);
 
 int bits_for(int64_t x);
+
+// The same LP run as lp_run as one cooperative persistent launch (lp_small.cu);
+// for graphs of at most p.small_nodes nodes and kLpSmallMaxEntries entries.
+bool lp_small_applicable(const DevGraph &g, const LpParams &p);
+LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight, int64_t nlabels,
+                      uint64_t seed, const LpParams &p, int64_t *nclusters_dev, uint8_t *label8);
 
 }  // namespace gp

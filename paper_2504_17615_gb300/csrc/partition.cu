@@ -282,7 +282,8 @@ int64_t refine_blocks(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t Lmax, i
   p.level = level; p.rounds = cfg.ref_rounds; p.subrounds = cfg.lp_subrounds;
   p.bound = Lmax; p.count_clusters = false; p.n_min = 0; p.dbg_max_subrounds = -1;
   p.prof_rate = PROF_REF_RATE; p.prof_accept = PROF_REF_ACCEPT;
-  p.prof_overflow = PROF_REF_OVERFLOW; p.prof_apply = PROF_REF_APPLY;
+  p.prof_overflow = PROF_REF_OVERFLOW; p.prof_apply = PROF_REF_APPLY; p.prof_small = PROF_REF_SMALL;
+  p.small_nodes = cfg.small_lp_nodes;
   DBuf<uint8_t> b8;
   if (k <= 255) {
     b8.reset(ctx, (size_t)g.n);
@@ -366,9 +367,15 @@ void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, u
     const DevGraph &cur = *G[L];
     DBuf<int32_t> cmap(ctx, (size_t)cur.n);
     LevelOut lo;
-    coarsen_level(ctx, cur, U, L + 1, seed, cfg, cmap.get(), nullptr, lo);
+    {
+      NvtxRange r("coarsen", L + 1);
+      coarsen_level(ctx, cur, U, L + 1, seed, cfg, cmap.get(), nullptr, lo);
+    }
     auto Gc = std::make_unique<DevGraph>();
-    contract_graph(ctx, cur, cmap.get(), lo.n_coarse, *Gc);
+    {
+      NvtxRange r("contract", L + 1);
+      contract_graph(ctx, cur, cmap.get(), lo.n_coarse, *Gc);
+    }
     gp_level_stats ls = lo.st;
     ls.n = cur.n;
     ls.n_next = lo.n_coarse;
@@ -382,6 +389,7 @@ void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, u
                    (__int128)ls.m_coarse * cfg.rho_den > (__int128)cfg.rho_num * ls.m_hat;
     if (ls.triggered) {
       auto Gs = std::make_unique<DevGraph>();
+      NvtxRange r("sparsify", L + 2);
       sparsify_graph(ctx, *Gc, ls.m_hat, L + 2, seed, cfg.sparsifier, *Gs, &ls);
       Gc = std::move(Gs);
     }
@@ -396,11 +404,17 @@ void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, u
   tm.mark(1);
   // initial partition of the coarsest graph
   DBuf<int32_t> blk(ctx, (size_t)G[L]->n);
-  initial_partition(ctx, *G[L], k, eps_ppm, seed, cfg.ip_trials, blk.get());
-  cut_and_weights(ctx, *G[L], blk.get(), k, &S.ip_cut, nullptr);
-  S.rebalance_moves = rebalance_blocks(ctx, *G[L], k, Lmax, blk.get());
+  {
+    NvtxRange r("initial");
+    initial_partition(ctx, *G[L], k, eps_ppm, seed, cfg.ip_trials, blk.get());
+    cut_and_weights(ctx, *G[L], blk.get(), k, &S.ip_cut, nullptr);
+    S.rebalance_moves = rebalance_blocks(ctx, *G[L], k, Lmax, blk.get());
+  }
   tm.mark(2);
-  refine_blocks(ctx, *G[L], k, Lmax, L + 1, seed, cfg, blk.get());
+  {
+    NvtxRange r("refine", L + 1);
+    refine_blocks(ctx, *G[L], k, Lmax, L + 1, seed, cfg, blk.get());
+  }
   for (int i = L - 1; i >= 0; i--) {
     DBuf<int32_t> fine;
     int32_t *dst;
@@ -410,6 +424,7 @@ void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, u
       fine.reset(ctx, (size_t)G[i]->n);
       dst = fine.get();
     }
+    NvtxRange r("refine", i + 1);
     project(ctx, G[i]->n, C[i].get(), blk.get(), dst);
     refine_blocks(ctx, *G[i], k, Lmax, i + 1, seed, cfg, dst);
     if (i > 0) blk = std::move(fine);

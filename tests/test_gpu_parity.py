@@ -261,10 +261,10 @@ def test_cut_and_project(gp, ctx):
 
 # ---------------------------------------------------------------- partition
 
-def _check_partition(gp, ctx, g, k, eps, seed, cfg_kw=None):
+def _check_partition(gp, ctx, g, k, eps, seed, cfg_kw=None, gpu_kw=None):
     cfg_kw = cfg_kw or {}
     dg = gp.DeviceGraph.from_host(g)
-    blocks, cut, st = ctx.gp_partition(dg, k, eps, seed, gp.default_config(**cfg_kw))
+    blocks, cut, st = ctx.gp_partition(dg, k, eps, seed, gp.default_config(**cfg_kw, **(gpu_kw or {})))
     r = orc.partition(g, k, eps, seed, orc.Config.default(**cfg_kw))
     assert r.rc == orc.OK
     assert cut == r.cut
@@ -446,3 +446,81 @@ def test_schedule_pins_on_gpu(gp, ctx, c):
         assert np.array_equal(blk.cpu().numpy(), want)
     else:
         raise AssertionError(call)
+
+
+# ------------------------------------- both LP drivers: persistent and per-phase
+#
+# Graphs up to gp_config.small_lp_nodes nodes run each LP call as one persistent
+# launch (every test above on small graphs goes that way by default);
+# small_lp_nodes = 0 forces the per-phase driver that large levels use.
+
+HOST_PATH = dict(small_lp_nodes=0)
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_coarsen_per_phase_driver_matches_oracle(gp, ctx, name):
+    g = GRAPHS[name]
+    W = int(g.vwgt.sum())
+    for U in (max(1, W // (160 * 2)), 6):
+        dg = gp.DeviceGraph.from_host(g)
+        cmap, nc, st, label = ctx.gp_coarsen(dg, U, 1, 7, gp.default_config(**HOST_PATH), want_label=True)
+        olabel, oncl, ost = orc.cluster(g, U, 1, 7)
+        assert np.array_equal(label.cpu().numpy(), olabel), f"labels differ ({name}, U={U})"
+        assert (st.lp_subrounds, st.lp_moves, st.clusters_lp, st.clusters_final) == \
+            (ost.lp_subrounds, ost.lp_moves, ost.clusters_lp, ost.clusters_final)
+
+
+@pytest.mark.parametrize("subs", [1, 3, 9])
+def test_lp_state_per_phase_driver(gp, ctx, subs):
+    g = GRAPHS["er_w"]
+    kw = dict(dbg_max_subrounds=subs, two_hop=0, isolated=0)
+    dg = gp.DeviceGraph.from_host(g)
+    for U in (5, 40):
+        _, nc, st, label = ctx.gp_coarsen(dg, U, 2, 3, gp.default_config(**kw, **HOST_PATH), want_label=True)
+        olabel, oncl, ost = orc.cluster(g, U, 2, 3, orc.Config.default(**kw))
+        assert np.array_equal(label.cpu().numpy(), olabel)
+        assert nc == oncl and st.lp_subrounds == ost.lp_subrounds
+
+
+@pytest.mark.parametrize("k", [2, 128, 300])
+def test_refine_per_phase_driver_matches_oracle(gp, ctx, k):
+    import torch
+    for g in (GRAPHS["er_w"], GRAPHS["rmat12"]):
+        Lmax = orc.lmax(int(g.vwgt.sum()), k, 30000)
+        blk = np.random.default_rng(k).integers(0, k, g.n).astype(np.int32)
+        blk, _ = orc.rebalance(g, k, Lmax, blk)
+        dg = gp.DeviceGraph.from_host(g)
+        t = torch.from_numpy(blk.copy()).cuda()
+        mv = ctx.gp_refine(dg, k, Lmax, 2, 13, t, gp.default_config(**HOST_PATH))
+        oblk, omv = orc.refine(g, k, Lmax, 2, 13, blk)
+        assert mv == omv and np.array_equal(t.cpu().numpy(), oblk)
+
+
+@pytest.mark.parametrize("name,k", [("er", 4), ("rmat12", 16), ("star", 2), ("dense", 6)])
+def test_partition_per_phase_driver_matches_oracle(gp, ctx, name, k):
+    _check_partition(gp, ctx, GRAPHS[name], k, 0.03, 2, gpu_kw=HOST_PATH)
+
+
+def test_partition_both_drivers_agree_on_c1(gp, ctx):
+    g = gg.er(65536, 524288, 1)
+    dg = gp.DeviceGraph.from_host(g)
+    b1, c1, s1 = ctx.gp_partition(dg, 2, 0.03, 1)
+    b2, c2, s2 = ctx.gp_partition(dg, 2, 0.03, 1, gp.default_config(**HOST_PATH))
+    assert c1 == c2 and np.array_equal(b1.cpu().numpy(), b2.cpu().numpy())
+
+
+def test_persistent_lp_wait_limit_gives_timeout_and_context_survives(gp, ctx):
+    """A grid-wide wait of the persistent LP kernel that runs out returns GP_ERR_TIMEOUT
+    (no trap, no hang); the context then works as before."""
+    g = GRAPHS["er"]
+    dg = gp.DeviceGraph.from_host(g)
+    ctx.gp_set_wait_limit(-1)  # every device-side wait gives up at once
+    try:
+        with pytest.raises(gp.GpError) as ei:
+            ctx.gp_coarsen(dg, 20, 1, 1)
+        assert ei.value.status == gp.GP_ERR_TIMEOUT
+    finally:
+        ctx.gp_set_wait_limit(0)
+    cmap, nc, _ = ctx.gp_coarsen(dg, 20, 1, 1)
+    ocmap, onc, _ = orc.coarsen(g, 20, 1, 1)
+    assert nc == onc and np.array_equal(cmap.cpu().numpy(), ocmap)
