@@ -20,7 +20,7 @@ enum RateMode { RATE_LP = 0, RATE_FAV = 1 };
 
 // LP runs on graphs up to this size use the persistent kernel of lp_small.cu
 // (gp_config.small_lp_nodes, default) and at most this many CSR entries.
-constexpr int32_t kLpSmallMaxNodes = 1 << 20;
+constexpr int32_t kLpSmallMaxNodes = 5 << 20;
 constexpr int64_t kLpSmallMaxEntries = (int64_t)1 << 26;
 // iterations of a device-side wait before it gives up (about seconds)
 constexpr long long kDefaultWaitSpins = 1ll << 25;

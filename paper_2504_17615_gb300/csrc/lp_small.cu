@@ -11,9 +11,12 @@
 // phases of a sub-round are separated by grid-wide barriers, and every block
 // takes the same stop decisions from the same global counters.
 //
-// Per sub-round:
-//   rate    warps rate the active nodes of degree <= 128 (a 256-slot table
-//           per warp), heavier nodes are listed and rated block by block
+// Per round, the nodes with neighbours are listed by (sub-round, degree
+// class) in two passes (count, scatter).  Per sub-round:
+//   rate    nodes of degree <= 8 are rated by 8-lane groups, <= 32 by a warp
+//           with one entry per lane, <= 128 by a warp with four entries per
+//           lane (equal labels summed in a small shared table, read back only
+//           by the lane that claimed the label's slot), larger ones by a block
 //   decide  a target whose snapshot weight plus all incoming weight fits the
 //           bound accepts its proposers outright; the others are resolved in
 //           (target, h32(PRIO), node) order, longest prefix (R7)
@@ -45,6 +48,8 @@ constexpr int kPBuckets = 4096;     // few-label overflow: priority buckets (top
 constexpr int kPCross = 1024;       // few-label overflow: crossing-bucket entries kept in shared memory
 constexpr int kPFewLabels = 256;    // labels up to this count: per-target overflow resolution
 constexpr int kPAggLabels = 4096;   // labels up to this count: weight updates aggregated per block
+constexpr int kPWeightSmem = 1024;  // refinement with labels up to this count: weights in shared memory
+constexpr int kPKeys = 64 * 4;      // (sub-round, degree class) lists of a round
 // resident blocks per SM of the persistent grid, and the pause between polls of a grid-wide wait
 #ifndef GP_PLP_BLOCKS_PER_SM
 #define GP_PLP_BLOCKS_PER_SM 3
@@ -82,7 +87,9 @@ struct PArgs {
   int4 *prop;            // [n] (node, target, own label, weight)
   int32_t *incoming;     // [nlabels], zero between sub-rounds
   uint8_t *acc;          // [n] per proposal: accepted
-  int32_t *heavy;        // [n]
+  int32_t *blist;        // [n] the round's nodes by (sub-round, degree class)
+  int32_t *bcnt, *bfill; // [2][kPKeys] list sizes and fill cursors (by round parity)
+  int32_t *boffs;        // [2][kPKeys + 1] list offsets
   uint64_t *ovk;         // [cap2] (target << 32 | priority)
   uint32_t *ovv;         // [cap2] node
   int32_t *ovi;          // [cap2] proposal index
@@ -269,6 +276,131 @@ __device__ void bitonic(uint64_t *k, uint32_t *v, int32_t *ix, int P) {
   }
 }
 
+// Rates the nodes list[0 .. count) with one node per G-lane group, up to E
+// entries per lane (degree <= G * E), summing equal labels in a 2 G E slot
+// table per group (keys tk, sums tv: the warp's 256-slot table split between
+// its groups).  A lane that claims a slot for a label speaks for it.  With
+// the label weights in shared memory (s_wl, refinement) every candidate is
+// checked against the bound up front; otherwise the leading candidate's
+// weight is read first, and the remaining candidates' weights only when it
+// does not fit (at most three passes).
+template <int G, int E>
+__device__ __forceinline__ void rate_list(const PArgs &a, PCount *c, const int32_t *list, int count, int gw,
+                                          int nw, int *tk, int *tv, uint64_t ktie, const int *s_wl,
+                                          unsigned long long &ue, unsigned long long &uv) {
+  constexpr int NV = 32 / G;
+  constexpr int TS = 2 * G * E;
+  constexpr int BITS = TS == 16 ? 4 : TS == 32 ? 5 : TS == 64 ? 6 : TS == 128 ? 7 : 8;
+  static_assert((1 << BITS) == TS && NV * TS <= kPSlots, "table size");
+  const int lane = (int)lane_id(), grp = lane / G, gl = lane % G;
+  const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
+  int *gk = tk + grp * TS, *gv = tv + grp * TS;
+  for (int i0 = gw * NV; i0 < count; i0 += nw * NV) {
+    const int i = i0 + grp;
+    const int v = i < count ? list[i] : -1;
+    int st = 0, deg = 0, own = -2, cv = 0;
+    if (v >= 0) {
+      st = a.xadj[v];
+      deg = a.xadj[v + 1] - st;
+      own = plabel(a, v);
+      cv = a.vwgt[v];
+    }
+    int L[E], w[E], slot[E], sum[E];
+    bool lead[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      const int j = gl + e * G;
+      const bool ok = j < deg;
+      const int u = ok ? a.adjncy[st + j] : 0;
+      w[e] = ok ? a.adjwgt[st + j] : 0;
+      L[e] = ok ? plabel(a, u) : -1;
+    }
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      slot[e] = -1;
+      lead[e] = false;
+      if (L[e] < 0) continue;
+      unsigned sl = ((unsigned)L[e] * 2654435761u) >> (32 - BITS);
+      for (int probe = 0; probe < TS; probe++) {  // bounded: at most G E labels in 2 G E slots
+        const int prev = atomicCAS(&gk[sl], -1, L[e]);
+        if (prev == -1) { lead[e] = true; break; }
+        if (prev == L[e]) break;
+        sl = (sl + 1) & (TS - 1);
+      }
+      slot[e] = (int)sl;
+      atomicAdd(&gv[sl], w[e]);
+    }
+    __syncwarp();
+    int own_loc = 0;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      sum[e] = lead[e] ? gv[slot[e]] : 0;
+      if (lead[e] && L[e] == own) own_loc = sum[e];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; e++)
+      if (lead[e]) { gk[slot[e]] = -1; gv[slot[e]] = 0; }
+    const int own_r = (int)__reduce_max_sync(gmask, (unsigned)own_loc);
+    bool alive[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      alive[e] = lead[e] && L[e] != own;
+      if (s_wl && alive[e]) alive[e] = (int64_t)s_wl[L[e]] + cv <= a.bound;
+    }
+    bool eager = s_wl != nullptr, searching = v >= 0;
+    unsigned best = 0xFFFFFFFFu;
+    for (int it = 0; it < 3; it++) {  // lazy pass, eager pass, one to find nothing left
+      if (!__any_sync(FULL, searching)) break;
+      if (eager && !s_wl) {
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (searching && alive[e] && (int64_t)a.weight[L[e]] + cv > a.bound) alive[e] = false;
+      }
+      unsigned rl = 0;
+#pragma unroll
+      for (int e = 0; e < E; e++)
+        if (searching && alive[e]) rl = max(rl, (unsigned)sum[e] + 1u);
+      const int r = (int)__reduce_max_sync(gmask, rl) - 1;
+      if (r < 0 || r <= own_r) searching = false;
+      unsigned hl = 0xFFFFFFFFu;
+#pragma unroll
+      for (int e = 0; e < E; e++)
+        if (searching && alive[e] && sum[e] == r) hl = min(hl, h32(ktie, (uint32_t)v, (uint32_t)L[e]));
+      const unsigned hmin = __reduce_min_sync(gmask, hl);
+      unsigned cl = 0xFFFFFFFFu;
+#pragma unroll
+      for (int e = 0; e < E; e++)
+        if (searching && alive[e] && sum[e] == r && h32(ktie, (uint32_t)v, (uint32_t)L[e]) == hmin)
+          cl = min(cl, (unsigned)L[e]);
+      const unsigned cL = __reduce_min_sync(gmask, cl);
+      if (eager) {
+        if (searching) { best = cL; searching = false; }
+      } else {
+        // the lane holding the leading candidate reads its weight
+        bool holder = false;
+#pragma unroll
+        for (int e = 0; e < E; e++) holder = holder || (searching && alive[e] && (unsigned)L[e] == cL);
+        const unsigned fits = holder && (int64_t)a.weight[cL] + cv <= a.bound ? 1u : 0u;
+        if (__reduce_or_sync(gmask, fits) && searching) { best = cL; searching = false; }
+#pragma unroll
+        for (int e = 0; e < E; e++) alive[e] = alive[e] && (unsigned)L[e] != cL;
+        eager = true;
+      }
+    }
+    if (gl == 0 && v >= 0) {
+      ue += deg;
+      uv += 1;
+      if (best != 0xFFFFFFFFu) propose(a, c, v, (int)best, own, cv);
+    }
+  }
+}
+
+// degree classes of the per-round lists: <= 8 (8 lanes per node), <= 32 (a
+// warp, one entry per lane), <= 128 (a warp, four entries per lane), larger
+// (a block)
+__device__ __forceinline__ int deg_class(int deg) { return deg <= 8 ? 0 : deg <= 32 ? 1 : deg <= kPLight ? 2 : 3; }
+
 // ---------------------------------------------------------- the kernel
 
 __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
@@ -281,6 +413,8 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
   __shared__ uint64_t s_ru[kPWarps];
   __shared__ long long s_ll[kPWarps];
   __shared__ unsigned s_h[256];
+  __shared__ int s_bc[kPKeys], s_bb[kPKeys], s_bo[kPKeys + 1];
+  __shared__ int s_wl[kPWeightSmem];
 
   const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -299,12 +433,78 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
   unsigned long long ue = 0, uv = 0;
   const bool few = a.nlabels <= kPFewLabels;
   const bool agg = !a.count_clusters && a.nlabels <= kPAggLabels;
+  const bool few_w = !a.count_clusters && a.nlabels <= kPWeightSmem;  // label weights in shared memory
 
   for (int r = 0; r < a.rounds && !stop; r++) {
     const uint64_t kact = stream_key(a.seed, a.tag_act, (uint32_t)a.level, (uint32_t)r);
     const uint64_t ktie = stream_key(a.seed, a.tag_tie, (uint32_t)a.level, (uint32_t)r);
     const uint64_t kprio = stream_key(a.seed, a.tag_prio, (uint32_t)a.level, (uint32_t)r);
     long long moved_round = 0;
+    if (a.count_clusters && ncl <= a.n_min) break;
+    if (a.dbg_max >= 0 && subs >= a.dbg_max) break;
+    // the round's lists: nodes with neighbours by (sub-round, degree class), in two passes
+    {
+      const int nkeys = a.S * 4;
+      int32_t *cnt = a.bcnt + (r & 1) * kPKeys;
+      int32_t *fill = a.bfill + (r & 1) * kPKeys;
+      int32_t *offs = a.boffs + (r & 1) * (kPKeys + 1);
+      if (blockIdx.x == 0) {  // the other parity's counters, for the next round
+        for (int t = threadIdx.x; t < kPKeys; t += blockDim.x) {
+          a.bcnt[((r + 1) & 1) * kPKeys + t] = 0;
+          a.bfill[((r + 1) & 1) * kPKeys + t] = 0;
+        }
+      }
+      for (int t = threadIdx.x; t < nkeys; t += blockDim.x) s_bc[t] = 0;
+      __syncthreads();
+      for (int v = gt; v < n; v += gthreads) {
+        const int deg = a.xadj[v + 1] - a.xadj[v];
+        if (deg == 0) continue;
+        const int sr = (int)(h32(kact, (uint32_t)v, 0) % (uint32_t)a.S);
+        atomicAdd(&s_bc[sr * 4 + deg_class(deg)], 1);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nkeys; t += blockDim.x)
+        if (s_bc[t]) atomicAdd(&cnt[t], s_bc[t]);
+      if (!grid_sync(a)) return;
+      // offsets (every block computes the same prefix), then the scatter in chunks
+      if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < nkeys; t++) { s_bo[t] = run; run += cnt[t]; }
+        s_bo[nkeys] = run;
+      }
+      __syncthreads();
+      if (blockIdx.x == 0)
+        for (int t = threadIdx.x; t <= nkeys; t += blockDim.x) offs[t] = s_bo[t];
+      for (int c0 = blockIdx.x * kPThreads * 4; c0 < n; c0 += gridDim.x * kPThreads * 4) {
+        for (int t = threadIdx.x; t < nkeys; t += blockDim.x) s_bc[t] = 0;
+        __syncthreads();
+        int key[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int v = c0 + q * kPThreads + (int)threadIdx.x;
+          key[q] = -1;
+          if (v < n) {
+            const int deg = a.xadj[v + 1] - a.xadj[v];
+            if (deg > 0) key[q] = (int)(h32(kact, (uint32_t)v, 0) % (uint32_t)a.S) * 4 + deg_class(deg);
+          }
+          if (key[q] >= 0) atomicAdd(&s_bc[key[q]], 1);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nkeys; t += blockDim.x) {
+          s_bb[t] = s_bc[t] ? s_bo[t] + atomicAdd(&fill[t], s_bc[t]) : 0;
+          s_bc[t] = 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (key[q] < 0) continue;
+          const int v = c0 + q * kPThreads + (int)threadIdx.x;
+          a.blist[s_bb[key[q]] + atomicAdd(&s_bc[key[q]], 1)] = v;
+        }
+        __syncthreads();
+      }
+      if (!grid_sync(a)) return;
+    }
     for (int s = 0; s < a.S; s++) {
       if (a.count_clusters && ncl <= a.n_min) { stop = true; break; }
       if (a.dbg_max >= 0 && subs >= a.dbg_max) { stop = true; break; }
@@ -315,60 +515,22 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
         nx->delta = 0; nx->moved = 0; nx->touched = 0;
       }
       // ---------------------------------------------------------- rate
-      for (int base = gw * 32; base < n; base += nw * 32) {
-        const int v = base + lane;
-        int deg = 0, st = 0;
-        bool act = false;
-        if (v < n) {
-          st = a.xadj[v];
-          deg = a.xadj[v + 1] - st;
-          act = deg > 0 && (int)(h32(kact, (uint32_t)v, 0) % (uint32_t)a.S) == s;
-        }
-        const bool hv = act && deg > kPLight;
-        const int hpos = warp_append(&c->nheavy, hv);
-        if (hv) a.heavy[hpos] = v;
-        unsigned m = __ballot_sync(FULL, act && !hv);
-        while (m) {
-          const int src = __ffs(m) - 1;
-          m &= m - 1;
-          const int u0 = __shfl_sync(FULL, v, src);
-          const int s0 = __shfl_sync(FULL, st, src);
-          const int d0 = __shfl_sync(FULL, deg, src);
-          const int own = plabel(a, u0);
-          const int cv = a.vwgt[u0];
-          for (int j = lane; j < d0; j += 32) {
-            const int L = plabel(a, a.adjncy[s0 + j]);
-            const int w = a.adjwgt[s0 + j];
-            unsigned sl = ((unsigned)L * 2654435761u) >> 24;
-            for (int probe = 0; probe < kPSlots; probe++) {  // bounded: at most 128 labels in 256 slots
-              const int prev = atomicCAS(&tk[sl], -1, L);
-              if (prev == -1 || prev == L) { atomicAdd(&tv[sl], w); break; }
-              sl = (sl + 1) & (kPSlots - 1);
-            }
-          }
-          __syncwarp();
-          int own_r, rmax;
-          const uint64_t best = choose(a, tk, tv, kPSlots, lane, 32, u0, own, cv, ktie,
-                                       [](int x) { return warp_max(x); },
-                                       [](uint64_t x) { return warp_min(x); }, own_r, rmax);
-          if (lane == 0) {
-            ue += d0;
-            uv += 1;
-            if (best != ~0ull) propose(a, c, u0, (int)(uint32_t)best, own, cv);
-          }
-          for (int t = lane; t < kPSlots; t += 32) { tk[t] = -1; tv[t] = 0; }
-          __syncwarp();
-        }
+      const int32_t *lo = a.boffs + (r & 1) * (kPKeys + 1) + s * 4;  // this sub-round's four lists
+      if (few_w) {
+        for (int t = threadIdx.x; t < (int)a.nlabels; t += blockDim.x) s_wl[t] = a.weight[t];
+        __syncthreads();
       }
-      if (!grid_sync(a)) return;
-      const int nheavy = *(volatile int *)&c->nheavy;
-      if (nheavy > 0) {
+      // nodes of degree > kPLight: a block each, tables in shared memory (or global beyond)
+      {
         int *htk = reinterpret_cast<int *>(area);
         int *htv = htk + kPHeavySlots;
-        for (int t = threadIdx.x; t < kPHeavySlots; t += blockDim.x) { htk[t] = -1; htv[t] = 0; }
-        __syncthreads();
-        for (int h = blockIdx.x; h < nheavy; h += gridDim.x) {
-          const int v = a.heavy[h];
+        const int h0 = lo[3], h1 = lo[4];
+        if (h1 > h0) {
+          for (int t = threadIdx.x; t < kPHeavySlots; t += blockDim.x) { htk[t] = -1; htv[t] = 0; }
+          __syncthreads();
+        }
+        for (int h = h0 + blockIdx.x; h < h1; h += gridDim.x) {
+          const int v = a.blist[h];
           const int st = a.xadj[v], deg = a.xadj[v + 1] - st;
           int bits = 1;
           while ((1 << bits) < 2 * deg) bits++;
@@ -401,8 +563,14 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
           for (int t = threadIdx.x; t < tsize; t += blockDim.x) { k2[t] = -1; v2[t] = 0; }
           __syncthreads();
         }
-        if (!grid_sync(a)) return;
       }
+      {
+        const int *wl = few_w ? s_wl : nullptr;
+        rate_list<32, 4>(a, c, a.blist + lo[2], lo[3] - lo[2], gw, nw, tk, tv, ktie, wl, ue, uv);
+        rate_list<32, 1>(a, c, a.blist + lo[1], lo[2] - lo[1], gw, nw, tk, tv, ktie, wl, ue, uv);
+        rate_list<8, 1>(a, c, a.blist + lo[0], lo[1] - lo[0], gw, nw, tk, tv, ktie, wl, ue, uv);
+      }
+      if (!grid_sync(a)) return;
       // -------------------------------------------------------- decide
       const int nprop = *(volatile int *)&c->nprop;
       for (int b0 = blockIdx.x * blockDim.x; b0 < nprop; b0 += gthreads) {
@@ -751,7 +919,10 @@ LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *w
   int64_t cap2 = 1;
   while (cap2 < n) cap2 <<= 1;
   DBuf<int4> prop(ctx, (size_t)n);
-  DBuf<int32_t> incoming(ctx, (size_t)nlabels), heavy(ctx, (size_t)n), ovi(ctx, (size_t)cap2);
+  DBuf<int32_t> incoming(ctx, (size_t)nlabels), blist(ctx, (size_t)n), ovi(ctx, (size_t)cap2);
+  DBuf<int32_t> bcnt(ctx, 2 * (size_t)kPKeys), bfill(ctx, 2 * (size_t)kPKeys), boffs(ctx, 2 * ((size_t)kPKeys + 1));
+  bcnt.zero();
+  bfill.zero();
   DBuf<uint8_t> acc(ctx, (size_t)n);
   DBuf<uint64_t> ovk(ctx, (size_t)cap2);
   DBuf<uint32_t> ovv(ctx, (size_t)cap2);
@@ -803,7 +974,8 @@ LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *w
   a.rounds = p.rounds; a.S = p.subrounds; a.dbg_max = p.dbg_max_subrounds; a.level = p.level;
   a.seed = seed; a.tag_act = p.tag_act; a.tag_tie = p.tag_tie; a.tag_prio = p.tag_prio;
   a.ncl0 = ncl0;
-  a.prop = prop.get(); a.incoming = incoming.get(); a.acc = acc.get(); a.heavy = heavy.get();
+  a.prop = prop.get(); a.incoming = incoming.get(); a.acc = acc.get(); a.blist = blist.get();
+  a.bcnt = bcnt.get(); a.bfill = bfill.get(); a.boffs = boffs.get();
   a.ovk = ovk.get(); a.ovv = ovv.get(); a.ovi = ovi.get(); a.ovps = ovps.get(); a.cap2 = cap2;
   a.depw = depw.get(); a.dkey = dkey.get(); a.ekeys = ekeys.get(); a.chist = chist.get();
   a.gtk = gtk.get(); a.gtv = gtv.get(); a.gstride = gstride;
