@@ -249,7 +249,8 @@ gp_status gp_cut(gp_ctx *ctx, const gp_graph *g, const int32_t *blocks, int32_t 
  * cudaMalloc, cudaFree or other allocation: its only scratch is one fixed
  * device array inside the library, present on every device that loads the
  * library until the process exits.
- *   g        graph in device memory (as for gp_cut)
+ *   g        graph in device memory (as for gp_cut); entries need rows:
+ *            m2 > 0 with n == 0 is GP_ERR_INVALID
  *   blocks   device, g->n block ids in [0, k)
  *   k        1 <= k <= GP_CUT_NOALLOC_MAX_K, else GP_ERR_INVALID
  *   stream   cudaStream_t the work is ordered on; the call synchronises it
@@ -338,9 +339,21 @@ typedef struct gp_response {
   gp_status status;
   int64_t cut;
   double queued_ms, run_ms, total_ms; /* submit to start, start to end, submit to end */
+  int64_t start_order;                /* 1 for the first request a worker took, 2 for the next, ... */
+  int64_t estimate_bytes;             /* the admission estimate of the request */
+  int64_t peak_reserved_bytes;        /* device memory its worker's pool held at most while it ran */
+  int64_t peak_used_bytes;            /* device memory it had allocated at most */
 } gp_response;
 gp_status gp_server_create(gp_server **out, int device, int32_t workers, int64_t hbm_budget_bytes,
                            const gp_config *cfg);
+/*
+ * Head-of-line bound: while the oldest queued request does not fit next to the
+ * requests in flight, younger requests that do fit may start ahead of it, but
+ * at most max_bypass of them (default 8); after that nothing else starts until
+ * the oldest one does.  A request therefore waits for at most max_bypass
+ * requests submitted after it.  Not an algorithm parameter.
+ */
+void gp_server_set_max_bypass(gp_server *srv, int32_t max_bypass);
 /* Queues a request; *ticket identifies it for gp_server_wait. */
 gp_status gp_server_submit(gp_server *srv, const gp_request *req, int64_t *ticket);
 /* Blocks until the request is done, fills *out and forgets the ticket (wait once per ticket). */

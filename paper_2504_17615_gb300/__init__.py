@@ -53,7 +53,9 @@ class gp_request(ctypes.Structure):
 
 class gp_response(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("cut", ctypes.c_int64), ("queued_ms", ctypes.c_double),
-                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("start_order", ctypes.c_int64),
+                ("estimate_bytes", ctypes.c_int64), ("peak_reserved_bytes", ctypes.c_int64),
+                ("peak_used_bytes", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -161,6 +163,7 @@ def _load():
             "gp_server_submit": (ctypes.c_int, [P, ctypes.POINTER(gp_request), ctypes.POINTER(i64)]),
             "gp_server_wait": (ctypes.c_int, [P, i64, ctypes.POINTER(gp_response)]),
             "gp_server_destroy": (None, [P]),
+            "gp_server_set_max_bypass": (None, [P, i32]),
             "gp_modularity": (ctypes.c_int, [P, ctypes.POINTER(gp_graph), P, i32, ctypes.POINTER(gp_modularity_stats)]),
         }
         for name, (res, args) in sig.items():
@@ -522,6 +525,10 @@ class Server:
             raise GpError(st, "gp_server_create failed")
         self.ptr = p.value
         self._live = {}
+
+    def set_max_bypass(self, max_bypass: int):
+        """At most this many younger requests may start ahead of the oldest queued one."""
+        self.lib.gp_server_set_max_bypass(self.ptr, int(max_bypass))
 
     def submit(self, g, k: int, eps: float, seed: int) -> int:
         """g: a host graph (numpy CSR with int32 ids and weights).  Returns a ticket."""

@@ -266,10 +266,11 @@ void contract_graph(gp_ctx *ctx, const DevGraph &g, const int32_t *cmap, int32_t
   const int mseg = read_scalar(ctx, maxseg.get());
   int bits = 1;
   while ((1 << bits) < 2 * mseg) bits++;
-  const int lblocks = ctx->num_sms * 4;
+  int lblocks = ctx->num_sms * 4;
   DBuf<int32_t> gk, gv;
   if ((1 << bits) > kBlockSmemSlots) {
     a.gstride = (int64_t)1 << bits;
+    lblocks = table_blocks(g.m2, a.gstride, lblocks);
     gk.reset(ctx, (size_t)(a.gstride * lblocks));
     gv.reset(ctx, (size_t)(a.gstride * lblocks));
     a.gkeys = gk.get();

@@ -228,6 +228,16 @@ struct TraceTimer {
 
 constexpr int kWarp = 32;
 
+// Blocks that get a private global hash table of `slots` int pairs, at most
+// `want`: the tables together stay within 8 bytes per CSR entry plus 16 MiB,
+// so scratch memory grows with the graph, not with its largest degree.
+inline int table_blocks(int64_t m2, int64_t slots, int want) {
+  const int64_t cap = 8 * m2 + ((int64_t)16 << 20);
+  int64_t b = cap / (slots * 8);
+  if (b > want) b = want;
+  return b < 1 ? 1 : (int)b;
+}
+
 inline int grid_for(int64_t items, int per_block, int cap) {
   int64_t g = (items + per_block - 1) / per_block;
   if (g < 1) g = 1;

@@ -45,7 +45,13 @@ struct RateArgs {
   int64_t gstride;
   unsigned long long *units;
   int wlabels;          // labels whose weights a launch may copy to shared memory (<= 256)
+  uint8_t *dirty;       // optional: per node, 0 = cannot move until a neighbour moves (rating skipped)
+  const int32_t *ccount;  // optional: the list holds ccount[key] records from offs[key] (compacted)
 };
+
+__device__ __forceinline__ int list_end(const RateArgs &a) {
+  return a.ccount ? a.offs[a.key] + a.ccount[a.key] : a.offs[a.key + 1];
+}
 
 __device__ __forceinline__ void add_units(unsigned long long *units, unsigned long long e,
                                           unsigned long long v, unsigned long long c,
@@ -127,17 +133,25 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
     s_tv[wib][t] = 0;
   }
   __syncwarp();
-  const int begin = a.offs[a.key], end = a.offs[a.key + 1];
+  const int begin = a.offs[a.key], end = list_end(a);
   const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
   for (int base = begin + wid * PER; base < end; base += nw * PER) {
     int v[U], st[U], deg[U], own[U], cv[U], L[U], w[U], u[U];
+    bool skip[U];
 #pragma unroll
     for (int q = 0; q < U; q++) {
       const int i = base + q * NV + grp;
       const int4 rec = i < end ? a.list[i] : make_int4(-1, 0, 0, 0);
       v[q] = rec.x; st[q] = rec.y; deg[q] = rec.z; cv[q] = rec.w;
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      // a clean node cannot move: neither its neighbours' labels nor its own changed since it
+      // last found no label rated above its own
+      skip[q] = a.dirty && v[q] >= 0 && !a.dirty[v[q]];
+      if (skip[q]) { v[q] = -1; deg[q] = 0; }
     }
 #pragma unroll
     for (int q = 0; q < U; q++) {
@@ -211,6 +225,14 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
     // node takes at most three passes.
     bool alive[U], searching[U], eager[U];
     unsigned best[U];
+    if (a.dirty) {
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        // no label rated above the own one, admissible or not: clean until a neighbour moves
+        const int rall = (int)__reduce_max_sync(gmask, (lead[q] && L[q] != own[q]) ? (unsigned)sum[q] : 0u);
+        if (gl == 0 && v[q] >= 0 && rall <= own_r[q]) a.dirty[v[q]] = 0;
+      }
+    }
 #pragma unroll
     for (int q = 0; q < U; q++) {
       alive[q] = lead[q] && L[q] != own[q];
@@ -274,6 +296,8 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
         } else if (MODE == RATE_LP) {
           a.prop[base + q * NV + grp] = make_int2(-1, 0);
         }
+      } else if (gl == 0 && skip[q] && MODE == RATE_LP) {
+        a.prop[base + q * NV + grp] = make_int2(-1, 0);
       }
     }
   }
@@ -291,13 +315,17 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
   for (int t = lane; t < kMedSlots; t += 32) { tk[t] = -1; tv[t] = 0; }
   __syncwarp();
   if (a.stop && *a.stop) return;
-  const int begin = a.offs[a.key], end = a.offs[a.key + 1];
+  const int begin = a.offs[a.key], end = list_end(a);
   const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
   for (int i = begin + wid; i < end; i += nw) {
     const int4 rec = a.list[i];
     const int v = rec.x, start = rec.y, deg = rec.z, cv = rec.w;
+    if (a.dirty && !a.dirty[v]) {  // clean: cannot move
+      if (MODE == RATE_LP && lane == 0) a.prop[i] = make_int2(-1, 0);
+      continue;
+    }
     const int own = label_of(a, v);
     for (int j = lane; j < deg; j += 32) {
       const int L = label_of(a, __ldcs(a.adjncy + start + j));
@@ -310,18 +338,20 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
       }
     }
     __syncwarp();
-    int own_loc = 0, rloc = -1, nc = 0;
+    int own_loc = 0, rloc = -1, nc = 0, rall = 0;
     for (int t = lane; t < kMedSlots; t += 32) {
       const int L = tk[t];
       if (L < 0) continue;
       const int r = tv[t];
       if (L == own) { own_loc = r; continue; }
       nc++;
+      rall = r > rall ? r : rall;
       if (MODE == RATE_LP && (int64_t)a.weight[L] + cv > a.bound) continue;
       rloc = r > rloc ? r : rloc;
     }
     const int own_r = warp_max(own_loc);
     const int rmax = warp_max(rloc);
+    if (a.dirty && warp_max(rall) <= own_r && lane == 0) a.dirty[v] = 0;
     ue += deg; uv += 1; uc += nc;
     if (!(rmax < 0 || (MODE == RATE_LP && rmax <= own_r))) {
       uint64_t packed = ~0ull;
@@ -376,13 +406,17 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
   if (a.stop && *a.stop) return;
   for (int t = threadIdx.x; t < kLargeSmemSlots; t += blockDim.x) { s_k[t] = -1; s_v[t] = 0; }
   __syncthreads();
-  const int begin = a.offs[a.key], end = a.offs[a.key + 1];
+  const int begin = a.offs[a.key], end = list_end(a);
   int *gk = a.gkeys ? a.gkeys + (int64_t)blockIdx.x * a.gstride : nullptr;
   int *gv = a.gvals ? a.gvals + (int64_t)blockIdx.x * a.gstride : nullptr;
   unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
   for (int i = begin + (int)blockIdx.x; i < end; i += (int)gridDim.x) {
     const int4 rec = a.list[i];
     const int v = rec.x, start = rec.y, deg = rec.z, cv = rec.w;
+    if (a.dirty && !a.dirty[v]) {  // clean: cannot move (uniform in the block)
+      if (MODE == RATE_LP && threadIdx.x == 0) a.prop[i] = make_int2(-1, 0);
+      continue;
+    }
     const int own = label_of(a, v);
     int bits = 1;
     while ((1 << bits) < 2 * deg) bits++;
@@ -401,18 +435,23 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
       }
     }
     __syncthreads();
-    int own_loc = 0, rloc = -1, nc = 0;
+    int own_loc = 0, rloc = -1, nc = 0, rall = 0;
     for (int t = threadIdx.x; t < tsize; t += blockDim.x) {
       const int L = tk[t];
       if (L < 0) continue;
       const int r = tv[t];
       if (L == own) { own_loc = r; continue; }
       nc++;
+      rall = r > rall ? r : rall;
       if (MODE == RATE_LP && (int64_t)a.weight[L] + cv > a.bound) continue;
       rloc = r > rloc ? r : rloc;
     }
     const int own_r = block_max_i32(own_loc, s_ri);
     const int rmax = block_max_i32(rloc, s_ri);
+    if (a.dirty) {
+      const int ra = block_max_i32(rall, s_ri);
+      if (ra <= own_r && threadIdx.x == 0) a.dirty[v] = 0;
+    }
     uc += nc;
     if (threadIdx.x == 0) { ue += deg; uv += 1; }
     if (!(rmax < 0 || (MODE == RATE_LP && rmax <= own_r))) {
@@ -522,6 +561,67 @@ __global__ void __launch_bounds__(kThreads) k_bucket_scatter(BucketArgs b, int n
   }
 }
 
+// ------------------------------------------------------ clean nodes
+//
+// Refinement keeps a flag per node: a node whose rating found no label rated
+// above its own (admissible or not) cannot propose until one of its
+// neighbours moves, so it is left out of the rating lists until then.
+
+// The dirty records of the sub-round's buckets k0 .. k1-1, packed from the
+// start of each bucket's range; ccount[key] receives the bucket's count.
+__global__ void __launch_bounds__(kThreads) k_compact_dirty(const int4 *list, const int32_t *offs, int k0, int k1,
+                                                            const uint8_t *dirty, int4 *clist, int32_t *ccount,
+                                                            const int *stop) {
+  if (stop && *stop) return;
+  const int begin = offs[k0], end = offs[k1];
+  const int lane = (int)lane_id();
+  for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += gridDim.x * blockDim.x) {
+    const int i = base + (int)threadIdx.x;
+    int b = -1;
+    int4 rec = make_int4(0, 0, 0, 0);
+    if (i < end) {
+      b = k0;
+      while (b + 1 < k1 && offs[b + 1] <= i) b++;
+      rec = list[i];
+      if (!dirty[rec.x]) b = -1;
+    }
+    const unsigned peers = __match_any_sync(FULL, b >= 0 ? b : -1 - lane);
+    if (b >= 0) {
+      const int leader = __ffs(peers) - 1;
+      int pos = 0;
+      if (lane == leader) pos = atomicAdd(&ccount[b], __popc(peers));
+      pos = __shfl_sync(peers, pos, leader);
+      clist[offs[b] + pos + __popc(peers & lanemask_lt())] = rec;
+    }
+  }
+}
+
+// Every applied move makes its node and the node's neighbours dirty (a warp
+// per move reads the row).
+__global__ void __launch_bounds__(kThreads) k_mark_dirty(const int4 *mov, int nmov, const uint64_t *ov_key,
+                                                         const uint32_t *ov_val, const uint8_t *ov_acc, int nov,
+                                                         const uint64_t *cutoff, uint64_t kprio,
+                                                         const int32_t *xadj, const int32_t *adjncy,
+                                                         uint8_t *dirty) {
+  const int lane = (int)lane_id();
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int total = nmov + nov;
+  for (int t = wid; t < total; t += nw) {
+    int v;
+    if (t < nmov) {
+      v = mov[t].x;
+    } else {
+      if (!ov_acc[t - nmov]) continue;
+      v = (int)ov_val[t - nmov];
+    }
+    if (cutoff && ((((uint64_t)h32(kprio, (uint32_t)v, 0)) << 32) | (uint32_t)v) >= *cutoff) continue;
+    const int e0 = xadj[v], e1 = xadj[v + 1];
+    if (lane == 0) dirty[v] = 1;
+    for (int e = e0 + lane; e < e1; e += 32) dirty[adjncy[e]] = 1;
+  }
+}
+
 // ------------------------------------------------------------- acceptance
 
 struct Counters {
@@ -546,7 +646,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const int4 *list, const int
                                                      const int32_t *weight, const int32_t *incoming,
                                                      int64_t bound, int4 *mov,
                                                      uint64_t *ov_key, uint32_t *ov_val, Counters *cnt,
-                                                     uint64_t kprio) {
+                                                     uint64_t kprio, const int32_t *ccount) {
   __shared__ int s_a[kWarpsPerBlock + 1], s_o[kWarpsPerBlock + 1];
   if (cnt->stop) return;
   const int begin = offs[k0], end = offs[k1];
@@ -556,7 +656,13 @@ __global__ void __launch_bounds__(kThreads) k_decide(const int4 *list, const int
     const int i = base + (int)threadIdx.x;
     bool acc = false, over = false;
     int v = 0, K = -1, own = 0, c = 0;
-    if (i < end) {
+    bool live = i < end;
+    if (live && ccount) {  // compacted lists: positions past a bucket's count hold nothing
+      int b = k0;
+      while (b + 1 < k1 && offs[b + 1] <= i) b++;
+      live = i < offs[b] + ccount[b];
+    }
+    if (live) {
       const int2 pr = prop[i];
       K = pr.x;
       if (K >= 0) {
@@ -884,6 +990,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
     if (mv) {
       a.label[v] = K;
       if (a.label8) a.label8[v] = (uint8_t)K;
+
       if (a.nshared) {
         atomicAdd(&s_dw[K], c);
         atomicSub(&s_dw[own], c);
@@ -1063,6 +1170,7 @@ void make_tables(gp_ctx *ctx, const DevGraph &g, RateTables &t) {
   t.blocks = ctx->num_sms * 4;
   if ((1 << bits) > kLargeSmemSlots) {
     t.stride = (int64_t)1 << bits;
+    t.blocks = table_blocks(g.m2, t.stride, t.blocks);
     t.gkeys.reset(ctx, (size_t)(t.stride * t.blocks));
     t.gvals.reset(ctx, (size_t)(t.stride * t.blocks));
     t.gkeys.fill_bytes(0xFF);
@@ -1173,6 +1281,18 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
   }
   DBuf<Counters> counters(ctx, 1);
   Counters *C = counters.get();
+  // refinement: nodes that must be rated (all at first; a node with no label rated above its
+  // own is left out until a neighbour moves: it cannot propose, so results are unchanged)
+  const bool use_dirty = !p.count_clusters;
+  DBuf<uint8_t> dirty;
+  DBuf<int4> clist;
+  DBuf<int32_t> ccount;
+  if (use_dirty) {
+    dirty.reset(ctx, (size_t)n);
+    dirty.fill_bytes(1);
+    clist.reset(ctx, (size_t)n);
+    ccount.reset(ctx, (size_t)nkeys);
+  }
   // the 2.5x cap (clustering): departure weight and latest key per cluster, emptying keys
   DBuf<int32_t> cap_w;
   DBuf<unsigned long long> cap_k;
@@ -1226,6 +1346,19 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       a.bound = p.bound; a.ktie = ktie; a.prop = prop.get(); a.incoming = incoming.get();
       a.stop = &C->stop; a.units = units_rate; a.label8 = label8;
       a.wlabels = label8 ? (int)nlabels : 0;
+      a.dirty = dirty.get();
+      if (use_dirty) {
+        const int k0c = s * kNumBuckets;
+        GP_CUDA(cudaMemsetAsync(ccount.get() + k0c, 0, sizeof(int32_t) * kNumBuckets, ctx->stream));
+        const int act = hoffs[k0c + kNumBuckets] - hoffs[k0c];
+        if (act > 0) {
+          k_compact_dirty<<<grid_for(act, kThreads, grid), kThreads, 0, ctx->stream>>>(
+              list.get(), offs.get(), k0c, k0c + kNumBuckets, dirty.get(), clist.get(), ccount.get(), &C->stop);
+          GP_LAUNCH_CHECK();
+        }
+        a.list = clist.get();
+        a.ccount = ccount.get();
+      }
       {
         ProfScope ps(ctx, p.prof_rate);
         int hcnt[kNumBuckets];
@@ -1236,9 +1369,9 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       const int active = hoffs[k1] - hoffs[k0];
       {
         ProfScope ps(ctx, p.prof_accept);
-        k_decide<<<grid_for(active, kThreads, grid), kThreads, 0, ctx->stream>>>(list.get(), offs.get(), k0, k1, prop.get(), weight,
-                                                      incoming.get(), p.bound, mov.get(),
-                                                      ov_key.get(), ov_val.get(), C, kprio);
+        k_decide<<<grid_for(active, kThreads, grid), kThreads, 0, ctx->stream>>>(
+            use_dirty ? clist.get() : list.get(), offs.get(), k0, k1, prop.get(), weight, incoming.get(), p.bound,
+            mov.get(), ov_key.get(), ov_val.get(), C, kprio, use_dirty ? ccount.get() : nullptr);
         GP_LAUNCH_CHECK();
       }
       Counters hdr;
@@ -1300,6 +1433,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         aa.weight = weight; aa.incoming = incoming.get(); aa.label8 = label8;
         aa.nshared = agg ? (int)nlabels : 0; aa.cnt = C;
         aa.kprio = kprio;
+
         const int ga = grid_for((int64_t)nmov + nov, kThreads, grid);
         // the 2.5x cap: only when the accepted moves could empty more than D clusters
         const int64_t D = hdr.nclusters - p.n_min;
@@ -1330,6 +1464,12 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         if (nmov + nov > 0) {
           k_apply<<<ga, kThreads, sizeof(int) * aa.nshared, ctx->stream>>>(aa);
           GP_LAUNCH_CHECK();
+          if (use_dirty) {
+            k_mark_dirty<<<grid_for((int64_t)(nmov + nov) * 32, kThreads, grid), kThreads, 0, ctx->stream>>>(
+                mov.get(), nmov, ov_key.get(), ov_val.get(), ov_acc.get(), nov, aa.cutoff, kprio, g.xadj, g.adjncy,
+                dirty.get());
+            GP_LAUNCH_CHECK();
+          }
         }
         const int64_t count_labels = p.count_clusters ? nlabels : 0;
         const int gc = grid_for(std::max<int64_t>((int64_t)nmov + nov, count_labels / 4), kThreads, grid);

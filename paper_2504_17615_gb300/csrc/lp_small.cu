@@ -30,6 +30,7 @@
 // Every grid barrier waits with an iteration limit; when it runs out the
 // kernel records GP_ERR_TIMEOUT in a status word and every block returns.
 #include "lp.cuh"
+#include "lp_rate.cuh"
 
 #include <algorithm>
 
@@ -101,6 +102,7 @@ struct PArgs {
   unsigned *chist;       // [8][256] cap select histograms
   int32_t *gtk, *gtv;    // per-block global tables for heavy nodes beyond kPHeavySlots
   int64_t gstride;
+  int hblocks;           // the first hblocks blocks rate the heavy nodes (one table each)
   PCount *cnt;           // [3]
   unsigned *bar;         // [0] arrivals, [1] generation
   int *status;
@@ -276,25 +278,17 @@ __device__ void bitonic(uint64_t *k, uint32_t *v, int32_t *ix, int P) {
   }
 }
 
-// Rates the nodes list[0 .. count) with one node per G-lane group, up to E
-// entries per lane (degree <= G * E), summing equal labels in a 2 G E slot
-// table per group (keys tk, sums tv: the warp's 256-slot table split between
-// its groups).  A lane that claims a slot for a label speaks for it.  With
-// the label weights in shared memory (s_wl, refinement) every candidate is
-// checked against the bound up front; otherwise the leading candidate's
-// weight is read first, and the remaining candidates' weights only when it
-// does not fit (at most three passes).
+// Rates the nodes list[0 .. count), one node per G-lane group with up to E
+// entries per lane (rate_group of lp_rate.cuh), and proposes the moves.
 template <int G, int E>
 __device__ __forceinline__ void rate_list(const PArgs &a, PCount *c, const int32_t *list, int count, int gw,
                                           int nw, int *tk, int *tv, uint64_t ktie, const int *s_wl,
                                           unsigned long long &ue, unsigned long long &uv) {
   constexpr int NV = 32 / G;
-  constexpr int TS = 2 * G * E;
-  constexpr int BITS = TS == 16 ? 4 : TS == 32 ? 5 : TS == 64 ? 6 : TS == 128 ? 7 : 8;
-  static_assert((1 << BITS) == TS && NV * TS <= kPSlots, "table size");
+  constexpr int TS = GroupTable<G, E>::TS;
+  static_assert(NV * TS <= kPSlots, "table size");
   const int lane = (int)lane_id(), grp = lane / G, gl = lane % G;
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
-  int *gk = tk + grp * TS, *gv = tv + grp * TS;
   for (int i0 = gw * NV; i0 < count; i0 += nw * NV) {
     const int i = i0 + grp;
     const int v = i < count ? list[i] : -1;
@@ -305,89 +299,10 @@ __device__ __forceinline__ void rate_list(const PArgs &a, PCount *c, const int32
       own = plabel(a, v);
       cv = a.vwgt[v];
     }
-    int L[E], w[E], slot[E], sum[E];
-    bool lead[E];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-      const int j = gl + e * G;
-      const bool ok = j < deg;
-      const int u = ok ? a.adjncy[st + j] : 0;
-      w[e] = ok ? a.adjwgt[st + j] : 0;
-      L[e] = ok ? plabel(a, u) : -1;
-    }
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-      slot[e] = -1;
-      lead[e] = false;
-      if (L[e] < 0) continue;
-      unsigned sl = ((unsigned)L[e] * 2654435761u) >> (32 - BITS);
-      for (int probe = 0; probe < TS; probe++) {  // bounded: at most G E labels in 2 G E slots
-        const int prev = atomicCAS(&gk[sl], -1, L[e]);
-        if (prev == -1) { lead[e] = true; break; }
-        if (prev == L[e]) break;
-        sl = (sl + 1) & (TS - 1);
-      }
-      slot[e] = (int)sl;
-      atomicAdd(&gv[sl], w[e]);
-    }
-    __syncwarp();
-    int own_loc = 0;
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-      sum[e] = lead[e] ? gv[slot[e]] : 0;
-      if (lead[e] && L[e] == own) own_loc = sum[e];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int e = 0; e < E; e++)
-      if (lead[e]) { gk[slot[e]] = -1; gv[slot[e]] = 0; }
-    const int own_r = (int)__reduce_max_sync(gmask, (unsigned)own_loc);
-    bool alive[E];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-      alive[e] = lead[e] && L[e] != own;
-      if (s_wl && alive[e]) alive[e] = (int64_t)s_wl[L[e]] + cv <= a.bound;
-    }
-    bool eager = s_wl != nullptr, searching = v >= 0;
-    unsigned best = 0xFFFFFFFFu;
-    for (int it = 0; it < 3; it++) {  // lazy pass, eager pass, one to find nothing left
-      if (!__any_sync(FULL, searching)) break;
-      if (eager && !s_wl) {
-#pragma unroll
-        for (int e = 0; e < E; e++)
-          if (searching && alive[e] && (int64_t)a.weight[L[e]] + cv > a.bound) alive[e] = false;
-      }
-      unsigned rl = 0;
-#pragma unroll
-      for (int e = 0; e < E; e++)
-        if (searching && alive[e]) rl = max(rl, (unsigned)sum[e] + 1u);
-      const int r = (int)__reduce_max_sync(gmask, rl) - 1;
-      if (r < 0 || r <= own_r) searching = false;
-      unsigned hl = 0xFFFFFFFFu;
-#pragma unroll
-      for (int e = 0; e < E; e++)
-        if (searching && alive[e] && sum[e] == r) hl = min(hl, h32(ktie, (uint32_t)v, (uint32_t)L[e]));
-      const unsigned hmin = __reduce_min_sync(gmask, hl);
-      unsigned cl = 0xFFFFFFFFu;
-#pragma unroll
-      for (int e = 0; e < E; e++)
-        if (searching && alive[e] && sum[e] == r && h32(ktie, (uint32_t)v, (uint32_t)L[e]) == hmin)
-          cl = min(cl, (unsigned)L[e]);
-      const unsigned cL = __reduce_min_sync(gmask, cl);
-      if (eager) {
-        if (searching) { best = cL; searching = false; }
-      } else {
-        // the lane holding the leading candidate reads its weight
-        bool holder = false;
-#pragma unroll
-        for (int e = 0; e < E; e++) holder = holder || (searching && alive[e] && (unsigned)L[e] == cL);
-        const unsigned fits = holder && (int64_t)a.weight[cL] + cv <= a.bound ? 1u : 0u;
-        if (__reduce_or_sync(gmask, fits) && searching) { best = cL; searching = false; }
-#pragma unroll
-        for (int e = 0; e < E; e++) alive[e] = alive[e] && (unsigned)L[e] != cL;
-        eager = true;
-      }
-    }
+    int nc = 0;
+    const unsigned best = rate_group<G, E, false>(a.adjncy, a.adjwgt, a.label, a.label8, a.weight, s_wl, a.bound,
+                                                  ktie, v, st, deg, own, cv, tk + grp * TS, tv + grp * TS, gmask,
+                                                  gl, false, nc);
     if (gl == 0 && v >= 0) {
       ue += deg;
       uv += 1;
@@ -529,7 +444,7 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
           for (int t = threadIdx.x; t < kPHeavySlots; t += blockDim.x) { htk[t] = -1; htv[t] = 0; }
           __syncthreads();
         }
-        for (int h = h0 + blockIdx.x; h < h1; h += gridDim.x) {
+        for (int h = h0 + blockIdx.x; h < h1 && (int)blockIdx.x < a.hblocks; h += a.hblocks) {
           const int v = a.blist[h];
           const int st = a.xadj[v], deg = a.xadj[v + 1] - st;
           int bits = 1;
@@ -949,10 +864,12 @@ LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *w
   while ((1 << bits) < 2 * maxdeg) bits++;
   DBuf<int32_t> gtk, gtv;
   int64_t gstride = 0;
+  int hblocks = grid;  // blocks that rate the nodes of degree > kPLight
   if ((1 << bits) > kPHeavySlots) {
     gstride = (int64_t)1 << bits;
-    gtk.reset(ctx, (size_t)(gstride * grid));
-    gtv.reset(ctx, (size_t)(gstride * grid));
+    hblocks = table_blocks(g.m2, gstride, grid);
+    gtk.reset(ctx, (size_t)(gstride * hblocks));
+    gtv.reset(ctx, (size_t)(gstride * hblocks));
     gtk.fill_bytes(0xFF);
     gtv.zero();
   }
@@ -978,7 +895,7 @@ LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *w
   a.bcnt = bcnt.get(); a.bfill = bfill.get(); a.boffs = boffs.get();
   a.ovk = ovk.get(); a.ovv = ovv.get(); a.ovi = ovi.get(); a.ovps = ovps.get(); a.cap2 = cap2;
   a.depw = depw.get(); a.dkey = dkey.get(); a.ekeys = ekeys.get(); a.chist = chist.get();
-  a.gtk = gtk.get(); a.gtv = gtv.get(); a.gstride = gstride;
+  a.gtk = gtk.get(); a.gtv = gtv.get(); a.gstride = gstride; a.hblocks = hblocks;
   a.cnt = dc->cnt; a.bar = dc->bar; a.status = &dc->status;
   a.spin_cap = ctx->wait_spins > 0 ? ctx->wait_spins : (ctx->wait_spins == 0 ? kDefaultWaitSpins : -1);
   a.out = &dc->out;

@@ -106,7 +106,7 @@ extern "C" gp_status gp_cut_noalloc(const gp_graph *g, const int32_t *blocks, in
   if (!g || !cut || k < 1 || g->n < 0 || g->m2 < 0 || g->m2 >= ((int64_t)1 << 31)) return GP_ERR_INVALID;
   if (k > kMaxK) return GP_ERR_INVALID;  // the fixed scratch holds at most GP_CUT_NOALLOC_MAX_K blocks
   if (g->n > 0 && (!g->xadj || !g->vwgt || !blocks)) return GP_ERR_INVALID;
-  if (g->m2 > 0 && (!g->adjncy || !g->adjwgt)) return GP_ERR_INVALID;
+  if (g->m2 > 0 && (g->n == 0 || !g->adjncy || !g->adjwgt)) return GP_ERR_INVALID;  // entries need rows
   gp_status st = GP_OK;
   unsigned long long *s = scratch_on_current_device(&st);
   if (!s) return st;

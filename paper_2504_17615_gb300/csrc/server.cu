@@ -20,12 +20,20 @@ struct Job {
   Clock::time_point t_submit, t_start, t_end;
   gp_status status = GP_OK;
   int64_t cut = 0;
+  int64_t order = 0;     // admission order
+  int32_t bypassed = 0;  // younger requests admitted while this one headed the queue
+  int64_t peak_reserved = 0, peak_used = 0;
   bool done = false;
 };
 
+// Device memory a partition request is admitted with: four times its CSR
+// (input copy, contraction segments, coarse graph, sparsified graph), the
+// hash tables of high-degree nodes (at most 8 bytes per entry plus 16 MiB),
+// 128 bytes per node (LP state, lists, the initial partitioner's trial state)
+// and 64 MiB; the served test checks every request's measured peak against it.
 int64_t estimate(const gp_request &r) {
   const int64_t csr = 4 * ((int64_t)r.n + 1) + 8 * r.m2 + 4 * (int64_t)r.n;
-  return 4 * csr + 64 * (int64_t)r.n + ((int64_t)64 << 20);
+  return 4 * csr + 8 * r.m2 + 128 * (int64_t)r.n + ((int64_t)80 << 20);
 }
 
 double ms(Clock::time_point a, Clock::time_point b) {
@@ -46,14 +54,25 @@ struct gp_server {
   std::condition_variable cv_work, cv_done;
   std::deque<int64_t> queue;
   std::unordered_map<int64_t, Job> jobs;
-  int64_t next_ticket = 1;
+  int64_t next_ticket = 1, next_order = 1;
+  int32_t max_bypass = 8;
   bool stop = false;
 
-  // the first queued job that fits next to those in flight (any job when none is in flight)
+  // The oldest queued job if it fits next to those in flight (any job when none
+  // is in flight); else a younger one that fits, as long as the oldest has been
+  // passed over fewer than max_bypass times.
   bool pick(int64_t *ticket) {
-    for (auto it = queue.begin(); it != queue.end(); ++it) {
-      const Job &j = jobs[*it];
-      if (running == 0 || in_use + j.est <= budget) {
+    if (queue.empty()) return false;
+    Job &head = jobs[queue.front()];
+    if (running == 0 || in_use + head.est <= budget) {
+      *ticket = queue.front();
+      queue.pop_front();
+      return true;
+    }
+    if (head.bypassed >= max_bypass) return false;
+    for (auto it = queue.begin() + 1; it != queue.end(); ++it) {
+      if (in_use + jobs[*it].est <= budget) {
+        head.bypassed++;
         *ticket = *it;
         queue.erase(it);
         return true;
@@ -75,17 +94,28 @@ struct gp_server {
         if (t == 0) return;  // stopping and nothing left
         Job &j = jobs[t];
         j.t_start = Clock::now();
+        j.order = next_order++;
         req = j.req;
         est = j.est;
         in_use += est;
         running++;
       }
+      // the worker's pool starts empty, so its high-water marks are this request's
+      if (ctx->pool) {
+        cudaMemPoolTrimTo(ctx->pool, 0);
+        unsigned long long zero = 0;
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReservedMemHigh, &zero);
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &zero);
+      }
       int64_t cut = 0;
       const gp_status st = gp_partition_host(ctx, req.n, req.m2, req.xadj, req.adjncy, req.vwgt, req.adjwgt,
                                              req.k, req.eps, req.seed, &cfg, req.blocks, &cut, nullptr);
+      unsigned long long hi_res = 0, hi_used = 0;
       if (ctx->pool) {
         cudaStreamSynchronize(ctx->stream);
-        cudaMemPoolTrimTo(ctx->pool, (size_t)(budget / (int64_t)ctxs.size()));
+        cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrReservedMemHigh, &hi_res);
+        cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &hi_used);
+        cudaMemPoolTrimTo(ctx->pool, 0);  // an idle worker holds no memory outside the budget
       }
       {
         std::lock_guard<std::mutex> lk(mu);
@@ -93,6 +123,8 @@ struct gp_server {
         j.t_end = Clock::now();
         j.status = st;
         j.cut = cut;
+        j.peak_reserved = (int64_t)hi_res;
+        j.peak_used = (int64_t)hi_used;
         j.done = true;
         in_use -= est;
         running--;
@@ -134,6 +166,12 @@ gp_status gp_server_create(gp_server **out, int device, int32_t workers, int64_t
   return GP_OK;
 }
 
+void gp_server_set_max_bypass(gp_server *s, int32_t max_bypass) {
+  if (!s || max_bypass < 0) return;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->max_bypass = max_bypass;
+}
+
 gp_status gp_server_submit(gp_server *s, const gp_request *req, int64_t *ticket) {
   if (!s || !req || !ticket) return GP_ERR_INVALID;
   if (req->n < 0 || req->m2 < 0 || req->m2 >= ((int64_t)1 << 31) || (req->n > 0 && (!req->xadj || !req->vwgt || !req->blocks)) ||
@@ -172,6 +210,10 @@ gp_status gp_server_wait(gp_server *s, int64_t ticket, gp_response *out) {
   out->queued_ms = ms(j.t_submit, j.t_start);
   out->run_ms = ms(j.t_start, j.t_end);
   out->total_ms = ms(j.t_submit, j.t_end);
+  out->start_order = j.order;
+  out->estimate_bytes = j.est;
+  out->peak_reserved_bytes = j.peak_reserved;
+  out->peak_used_bytes = j.peak_used;
   s->jobs.erase(it);
   lk.unlock();
   s->cv_done.notify_all();

@@ -52,6 +52,11 @@ def _requests(count, seed):
     return out
 
 
+def _est(g):
+    """The server's admission estimate (gp_response.estimate_bytes)."""
+    return 4 * (4 * (g.n + 1) + 8 * g.m2 + 4 * g.n) + 8 * g.m2 + 128 * g.n + (80 << 20)
+
+
 def _alone(ctx, g, k, eps, seed):
     blocks, cut, _ = ctx.gp_partition_host(g.n, g.m2, np.ascontiguousarray(g.xadj, dtype=np.int32),
                                            g.adjncy, g.vwgt, g.adjwgt, k, eps, seed)
@@ -79,7 +84,7 @@ def test_results_equal_alone_and_in_the_mix(gp, ctx):
 
 
 def test_requests_over_the_budget_are_refused(gp, ctx):
-    srv = gp.Server(0, workers=2, hbm_budget=80 << 20)
+    srv = gp.Server(0, workers=2, hbm_budget=120 << 20)
     try:
         big = gg.er(300000, 3000000, 1)
         with pytest.raises(gp.GpError) as e:
@@ -96,7 +101,7 @@ def test_requests_over_the_budget_are_refused(gp, ctx):
 
 def test_a_one_at_a_time_budget_serves_everything(gp, ctx):
     reqs = _requests(8, 9)
-    est = lambda g: 4 * (4 * (g.n + 1) + 8 * g.m2 + 4 * g.n) + 64 * g.n + (64 << 20)
+    est = _est
     budget = max(est(r[0]) for r in reqs) + (1 << 20)  # any two requests together exceed it
     srv = gp.Server(0, workers=4, hbm_budget=budget)
     try:
@@ -107,5 +112,50 @@ def test_a_one_at_a_time_budget_serves_everything(gp, ctx):
             b1, c1 = _alone(ctx, *r)
             assert resp.status == gp.GP_OK and cut == c1 and np.array_equal(blocks, b1)
         assert time.time() - t0 < 120
+    finally:
+        srv.close()
+
+
+def test_peak_memory_stays_within_the_admission_estimate(gp, ctx):
+    """Every request's measured peak (its worker's pool, emptied before the request) is at
+    most the estimate it was admitted with -- across the generator mix, including
+    Erdos-Renyi requests whose levels are sparsified (Alg. 1)."""
+    reqs = _requests(9, 11) + [(gg.er(200000, 1600000, 4), 8, 0.03, 5), (gg.er(60000, 600000, 6), 32, 0.03, 7)]
+    for g, k, eps, seed in reqs[-2:]:
+        _, _, st = ctx.gp_partition(gp.DeviceGraph.from_host(g), k, eps, seed)
+        assert any(st.lv[i].triggered for i in range(st.levels))
+    srv = gp.Server(0, workers=3)
+    try:
+        tickets = [srv.submit(*r) for r in reqs]
+        for r, t in zip(reqs, tickets):
+            _, _, resp = srv.wait(t)
+            assert resp.status == gp.GP_OK
+            assert resp.estimate_bytes == _est(r[0])
+            assert 0 < resp.peak_used_bytes <= resp.peak_reserved_bytes <= resp.estimate_bytes, \
+                (r[0].n, r[0].m2, resp.peak_used_bytes, resp.peak_reserved_bytes, resp.estimate_bytes)
+    finally:
+        srv.close()
+
+
+def test_oldest_request_waits_for_at_most_max_bypass_younger_ones(gp, ctx):
+    """A large request at the head of the queue that fits only alone is passed over by at
+    most max_bypass younger requests, however many keep arriving."""
+    big = (gg.er(200000, 1600000, 8), 16, 0.03, 3)
+    smalls = [(gg.er(20000, 160000, 100 + i), 8, 0.03, i + 1) for i in range(14)]
+    budget = _est(big[0]) + _est(smalls[0][0]) // 2  # the big one fits only when nothing else runs
+    assert 2 * _est(smalls[0][0]) <= budget
+    srv = gp.Server(0, workers=2, hbm_budget=budget)
+    srv.set_max_bypass(3)
+    try:
+        first = srv.submit(*smalls[0])
+        tb = srv.submit(*big)
+        rest = [srv.submit(*r) for r in smalls[1:]]
+        orders = {}
+        for t in [first, tb] + rest:
+            _, _, resp = srv.wait(t)
+            assert resp.status == gp.GP_OK
+            orders[t] = resp.start_order
+        younger_first = sum(1 for t in rest if orders[t] < orders[tb])
+        assert younger_first <= 3, (younger_first, orders)
     finally:
         srv.close()

@@ -75,3 +75,8 @@ def test_cut_noalloc_rejects_sizes_beyond_its_scratch_and_bad_blocks():
     blk[5] = 3
     st, cut, bw = _noalloc(fn, gp, dg, blk, 4, stream)
     assert st == gp.GP_OK and bw.sum() == g.n
+    # entries without rows (n == 0, m2 > 0) are rejected before any launch
+    bad = gp.gp_graph(0, dg.m2, None, dg.struct().adjncy, None, dg.struct().adjwgt)
+    out = ctypes.c_int64(0)
+    st = fn(ctypes.byref(bad), None, 4, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out), None)
+    assert st == gp.GP_ERR_INVALID
