@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kUpdUnroll = 4;
 constexpr int kChunkNodes = 64;
-constexpr int kMaxSmemBytes = 227 * 1024;
+constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // dynamic part (static shared variables use the rest)
 
 struct Sub {
   int32_t start, count;  // node list range
@@ -69,7 +69,22 @@ __device__ __forceinline__ unsigned long long gain_key(int64_t gain, int j) {
   return ((unsigned long long)(gain + 2147483648ll) << 32) | (0xFFFFFFFFu - (unsigned)j);
 }
 
-// chunk best over the live frontier nodes of chunk c (shared-memory state only)
+// 64-bit maximum / minimum over the warp with two 32-bit reductions each.
+__device__ __forceinline__ unsigned long long wmax_u64(unsigned long long x) {
+  const unsigned hi = (unsigned)(x >> 32);
+  const unsigned mh = __reduce_max_sync(0xFFFFFFFFu, hi);
+  const unsigned ml = __reduce_max_sync(0xFFFFFFFFu, hi == mh ? (unsigned)x : 0u);
+  return ((unsigned long long)mh << 32) | ml;
+}
+
+__device__ __forceinline__ unsigned long long wmin_u64(unsigned long long x) {
+  const unsigned hi = (unsigned)(x >> 32);
+  const unsigned mh = __reduce_min_sync(0xFFFFFFFFu, hi);
+  const unsigned ml = __reduce_min_sync(0xFFFFFFFFu, hi == mh ? (unsigned)x : 0xFFFFFFFFu);
+  return ((unsigned long long)mh << 32) | ml;
+}
+
+// chunk best over the live frontier nodes of chunk c (one warp)
 __device__ __forceinline__ void rescan_chunk(int c, int cnt, const int32_t *g, const uint8_t *st,
                                              unsigned long long *best) {
   const int lane = (int)lane_id();
@@ -82,14 +97,23 @@ __device__ __forceinline__ void rescan_chunk(int c, int cnt, const int32_t *g, c
       b = key > b ? key : b;
     }
   }
-  b = warp_max(b);
+  b = wmax_u64(b);
   if (lane == 0) best[c] = b;
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
+constexpr int kIpWarps = 4;  // warps per (subproblem, trial)
+
+// One block of kIpWarps warps per (subproblem, trial).  Warp 0 takes the
+// step's nodes from the chunk tournament; all warps then raise the
+// connections of the taken nodes' neighbours, scan for the fallback node and
+// add up the trial's cut.
+__global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
   extern __shared__ __align__(16) unsigned char dyn[];
-  const int lane = (int)lane_id();
+  __shared__ int s_nb;
+  __shared__ long long s_w1;
+  __shared__ unsigned long long s_red[kIpWarps];
+  const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
   const int si = blockIdx.x / a.trials, t = blockIdx.x % a.trials;
   const Sub S = a.subs[si];
   const int cnt = S.count, nch = (cnt + kChunkNodes - 1) / kChunkNodes;
@@ -114,49 +138,62 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
     st = a.gst + (int64_t)blockIdx.x * a.gnodes;
     if (a.cv16) cv = a.gcv + (int64_t)blockIdx.x * a.gnodes;
   }
-  for (int j = lane; j < cnt; j += 32) {
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     g[j] = -a.dpl[start + j];
     st[j] = S_FREE;
     if (cv) cv[j] = (uint16_t)a.cvl[start + j];
   }
-  for (int c = lane; c < nch; c += 32) best[c] = 0;
-  for (int c = lane; c < nsup; c += 32) sup[c] = 0;
-  __syncwarp();
+  for (int c = threadIdx.x; c < nch; c += blockDim.x) best[c] = 0;
+  for (int c = threadIdx.x; c < nsup; c += blockDim.x) sup[c] = 0;
+  __syncthreads();
   const uint64_t kip = stream_key(a.seed, TAG_IP, 0, (uint32_t)S.bid);
-  int64_t w1 = 0;
+  int64_t w1 = 0;  // warp 0's copy is the authoritative one; others read s_w1
   const int B = 1 + cnt / 1024;  // nodes per growing step
   int32_t *batch = a.gbatch + (int64_t)blockIdx.x * a.batch_cap;
-  while (w1 < S.T1) {
-    // extract up to B nodes in (gain desc, id asc) order; gains stay frozen until the step ends
-    int nb = 0;
-    while (nb < B && w1 < S.T1) {
-      unsigned long long b = 0;
-      for (int c = lane; c < nsup; c += 32) b = sup[c] > b ? sup[c] : b;
-      b = warp_max(b);
-      if (b == 0) break;
-      const int j = (int)(0xFFFFFFFFu - (unsigned)(b & 0xFFFFFFFFull));
-      const int cj = cv ? (int)cv[j] : a.cvl[start + j];
-      const bool fit = w1 + cj <= S.L1;
-      if (lane == 0) {
-        st[j] = fit ? S_ONE : S_OUT;  // S_OUT: cannot fit now, nor later
-        if (fit) batch[nb] = j;
-        if (a.trace && !fit) atomicAdd(a.trace + 2, 1ull);
+  for (;;) {
+    if (threadIdx.x == 0) s_w1 = w1;
+    __syncthreads();
+    w1 = s_w1;
+    if (w1 >= S.T1) break;
+    // warp 0: up to B nodes in (gain desc, id asc) order; gains stay frozen until the step ends
+    if (warp == 0) {
+      int nb = 0;
+      while (nb < B && w1 < S.T1) {
+        unsigned long long b = 0;
+        for (int c = lane; c < nsup; c += 32) b = sup[c] > b ? sup[c] : b;
+        b = wmax_u64(b);
+        if (b == 0) break;
+        const int j = (int)(0xFFFFFFFFu - (unsigned)(b & 0xFFFFFFFFull));
+        const int cj = cv ? (int)cv[j] : a.cvl[start + j];
+        const bool fit = w1 + cj <= S.L1;
+        if (lane == 0) {
+          st[j] = fit ? S_ONE : S_OUT;  // S_OUT: cannot fit now, nor later
+          if (fit) batch[nb] = j;
+          if (a.trace && !fit) atomicAdd(a.trace + 2, 1ull);
+        }
+        if (fit) { nb++; w1 += cj; }
+        __syncwarp();
+        const int c = j / kChunkNodes;
+        rescan_chunk(c, cnt, g, st, best);
+        const int s0 = (c / 32) * 32;  // the maximum over c's 32 chunks again
+        unsigned long long x = s0 + lane < nch ? best[s0 + lane] : 0;
+        x = wmax_u64(x);
+        if (lane == 0) sup[c / 32] = x;
+        __syncwarp();
       }
-      if (fit) { nb++; w1 += cj; }
-      __syncwarp();
-      const int c = j / kChunkNodes;
-      rescan_chunk(c, cnt, g, st, best);
-      const int s0 = (c / 32) * 32;  // the maximum over c's 32 chunks again
-      unsigned long long x = s0 + lane < nch ? best[s0 + lane] : 0;
-      x = warp_max(x);
-      if (lane == 0) sup[c / 32] = x;
-      __syncwarp();
+      if (lane == 0) {
+        s_nb = nb;
+        s_w1 = w1;
+        if (a.trace) atomicAdd(a.trace + 0, 1ull);
+      }
     }
-    if (a.trace && lane == 0) atomicAdd(a.trace + 0, 1ull);
-    if (nb == 0) {  // no frontier node fits: the smallest-hash node that fits
-      if (a.trace && lane == 0) atomicAdd(a.trace + 1, 1ull);
+    __syncthreads();
+    int nb = s_nb;
+    w1 = s_w1;
+    if (nb == 0) {  // no frontier node fits: the smallest-hash node that fits, found by all warps
+      if (a.trace && threadIdx.x == 0) atomicAdd(a.trace + 1, 1ull);
       unsigned long long m = ~0ull;
-      for (int jj = lane; jj < cnt; jj += 32) {
+      for (int jj = threadIdx.x; jj < cnt; jj += blockDim.x) {
         if (st[jj] != S_FREE) continue;
         const int cjj = cv ? (int)cv[jj] : a.cvl[start + jj];
         if (w1 + cjj > S.L1) continue;
@@ -164,16 +201,30 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
             ((unsigned long long)h32(kip, (uint32_t)a.vtx[start + jj], (uint32_t)t) << 32) | (unsigned)jj;
         m = key < m ? key : m;
       }
-      m = warp_min(m);
-      if (m == ~0ull) break;
-      const int j = (int)(unsigned)(m & 0xFFFFFFFFull);
-      w1 += cv ? (int)cv[j] : a.cvl[start + j];
-      if (lane == 0) { st[j] = S_ONE; batch[0] = j; }
-      nb = 1;
-      __syncwarp();
+      m = wmin_u64(m);
+      if (lane == 0) s_red[warp] = m;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned long long mm = s_red[0];
+        for (int q = 1; q < kIpWarps; q++) mm = s_red[q] < mm ? s_red[q] : mm;
+        if (mm == ~0ull) {
+          s_nb = -1;
+        } else {
+          const int j = (int)(unsigned)(mm & 0xFFFFFFFFull);
+          s_w1 = w1 + (cv ? (int)cv[j] : a.cvl[start + j]);
+          st[j] = S_ONE;
+          batch[0] = j;
+          s_nb = 1;
+        }
+      }
+      __syncthreads();
+      nb = s_nb;
+      if (nb < 0) break;
+      if (threadIdx.x == 0) w1 = s_w1;
     }
-    __syncwarp();
-    // neighbours of the step's nodes, over their concatenated local rows (32 nodes at a time)
+    if (threadIdx.x == 0) w1 = s_w1;
+    // neighbours of the step's nodes, over their concatenated local rows (32 nodes at a time),
+    // 32 * kUpdUnroll entries per warp and pass
     for (int b0 = 0; b0 < nb; b0 += 32) {
       int rs = 0, d = 0;
       if (b0 + lane < nb) {
@@ -188,7 +239,7 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
         if (lane >= o) incl += y;
       }
       const int excl = incl - d, total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      for (int f0 = 0; f0 < total; f0 += 32 * kUpdUnroll) {  // four entries per lane in flight
+      for (int f0 = warp * 32 * kUpdUnroll; f0 < total; f0 += kIpWarps * 32 * kUpdUnroll) {
         int idx[kUpdUnroll];
 #pragma unroll
         for (int r = 0; r < kUpdUnroll; r++) {
@@ -219,11 +270,11 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
         }
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
   // cut of this trial inside the subproblem
   unsigned long long cut = 0;
-  for (int jj = lane; jj < cnt; jj += 32) {
+  for (int jj = threadIdx.x; jj < cnt; jj += blockDim.x) {
     if (st[jj] != S_ONE) continue;
     const int p = start + jj;
     for (int e = a.lxadj[p]; e < a.lxadj[p + 1]; e++) {
@@ -232,9 +283,15 @@ __global__ void __launch_bounds__(32) k_ip_grow(IpArgs a) {
     }
   }
   cut = warp_sum(cut);
-  if (lane == 0) a.trial_cut[blockIdx.x] = (int64_t)cut;
+  if (lane == 0) s_red[warp] = cut;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long c = 0;
+    for (int q = 0; q < kIpWarps; q++) c += s_red[q];
+    a.trial_cut[blockIdx.x] = (int64_t)c;
+  }
   uint8_t *fl = a.flags + (int64_t)t * a.n + start;
-  for (int jj = lane; jj < cnt; jj += 32) fl[jj] = st[jj] == S_ONE;
+  for (int jj = threadIdx.x; jj < cnt; jj += blockDim.x) fl[jj] = st[jj] == S_ONE;
 }
 
 __global__ void k_sub_count(const int32_t *sp, const int32_t *vwgt, int n, int32_t *cnt, long long *w) {
@@ -470,7 +527,7 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
       GP_CUDA(cudaEventCreate(&e1));
       GP_CUDA(cudaEventRecord(e0, ctx->stream));
     }
-    k_ip_grow<<<nblocks, 32, smem_bytes, ctx->stream>>>(a);
+    k_ip_grow<<<nblocks, 32 * kIpWarps, smem_bytes, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
     if (trace) {
       GP_CUDA(cudaEventRecord(e1, ctx->stream));
