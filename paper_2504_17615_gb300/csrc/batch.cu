@@ -32,6 +32,7 @@ extern "C" gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32
       }
       ctx->workers.push_back(w);
     }
+    for (int i = 0; i < workers; i++) ctx->workers[i]->device_share = workers;
     // inputs may still be in flight on the caller's stream
     cudaEvent_t ready;
     GP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));

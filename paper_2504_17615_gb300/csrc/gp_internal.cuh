@@ -113,6 +113,7 @@ struct gp_ctx {
   double prof_host_bytes[gp::PROF_COUNT_] = {};  // algorithmic bytes of classes sized on the host
   std::vector<gp_ctx *> workers;                 // batch workers (own streams and pools)
   int64_t wait_spins = 0;                        // limit of device-side waits (0: default)
+  int device_share = 1;  // contexts sharing the device (batch / server workers): persistent grids shrink
 };
 
 namespace gp {

@@ -263,12 +263,17 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
           if (su == S_FREE || su == S_FRONT) {
             const int ng = atomicAdd(&g[e[r].x], 2 * e[r].y) + 2 * e[r].y;
             if (su == S_FREE) st[e[r].x] = S_FRONT;
-            const unsigned long long key = gain_key(ng, e[r].x);
-            atomicMax(&best[e[r].x / kChunkNodes], key);
-            atomicMax(&sup[e[r].x / (32 * kChunkNodes)], key);
+            atomicMax(&best[e[r].x / kChunkNodes], gain_key(ng, e[r].x));
           }
         }
       }
+    }
+    __syncthreads();
+    // the maxima over 32 chunks again, from the raised chunk maxima (one warp per group)
+    for (int sc = warp; sc < nsup; sc += kIpWarps) {
+      const int c = sc * 32 + lane;
+      const unsigned long long x = wmax_u64(c < nch ? best[c] : 0ull);
+      if (lane == 0) sup[sc] = x;
     }
     __syncthreads();
   }

@@ -827,7 +827,11 @@ LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *w
   int per_sm = 0;
   GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lp_persistent, kPThreads, kSmemBytes));
   GP_REQUIRE(per_sm >= 1, GP_ERR_CUDA, "persistent LP kernel does not fit on an SM");
-  const int grid = ctx->num_sms * std::min(per_sm, GP_PLP_BLOCKS_PER_SM);
+  // about one thread per node, at most the resident blocks of the device, divided among the
+  // contexts that share it (so that their persistent launches can run side by side)
+  const int full = ctx->num_sms * std::min(per_sm, GP_PLP_BLOCKS_PER_SM);
+  const int share = std::max(1, full / std::max(1, ctx->device_share));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(share, ((int64_t)n + kPThreads - 1) / kPThreads));
 
   int64_t ncl0 = 0;
   if (p.count_clusters && nclusters_dev) read_back(ctx, nclusters_dev, sizeof(int64_t), &ncl0);

@@ -121,27 +121,49 @@ __global__ void k_project(int n, const int32_t *cmap, const int32_t *coarse, int
     fine[v] = coarse[cmap[v]];
 }
 
+// cut = 1/2 sum over CSR entries whose endpoints lie in different blocks: a
+// warp walks 32 consecutive rows (one contiguous range of entries), finds each
+// entry's row among its lanes by a shuffle search, and keeps four entries per
+// lane in flight.
 template <typename B>
 __global__ void __launch_bounds__(256) k_cut(const int32_t *xadj, const int32_t *adjncy,
-                                             const int32_t *adjwgt, const B *blk, int n, int64_t m2,
+                                             const int32_t *adjwgt, const B *blk, int n,
                                              unsigned long long *cut) {
+  constexpr int R = 4;
   const int lane = (int)lane_id();
-  const int64_t chunk = 1024;
-  const int64_t nchunks = (m2 + chunk - 1) / chunk;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   unsigned long long s = 0;
-  for (int64_t c = wid; c < nchunks; c += nw) {
-    const int64_t e0 = c * chunk;
-    const int64_t e1 = e0 + chunk < m2 ? e0 + chunk : m2;
-    int row = 0;
-    if (lane == 0) row = row_of(xadj, n, e0);
-    row = __shfl_sync(FULL, row, 0);
-    int brow = -1, lastrow = -1;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-      while (row < n - 1 && (int64_t)xadj[row + 1] <= e) row++;
-      if (row != lastrow) { brow = blk[row]; lastrow = row; }
-      if (blk[adjncy[e]] != brow) s += (unsigned long long)adjwgt[e];
+  for (int64_t u0 = (int64_t)wid * 32; u0 < n; u0 += (int64_t)nw * 32) {
+    const int64_t u = u0 + lane;
+    const bool valid = u < n;
+    const int xe = valid ? xadj[u + 1] : 0x7FFFFFFF;
+    const int bu = valid ? (int)blk[u] : -1;
+    const int e0 = __shfl_sync(FULL, valid ? xadj[u] : 0, 0);
+    const int last = (int)((n - u0) < 32 ? (n - u0) : 32) - 1;
+    const int e1 = __shfl_sync(FULL, xe, last);
+    for (int f0 = e0; f0 < e1; f0 += 32 * R) {
+      int e[R], bo[R], v[R], w[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        e[r] = f0 + r * 32 + lane;
+        int q = 0;  // owner: lanes whose row ends at or before e
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int val = __shfl_sync(FULL, xe, q + step - 1);
+          if (val <= e[r]) q += step;
+        }
+        bo[r] = __shfl_sync(FULL, bu, q);
+      }
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const bool in = e[r] < e1;
+        v[r] = in ? __ldcs(adjncy + e[r]) : 0;
+        w[r] = in ? __ldcs(adjwgt + e[r]) : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < R; r++)
+        if (e[r] < e1 && (int)blk[v[r]] != bo[r]) s += (unsigned long long)w[r];
     }
   }
   s = warp_sum(s);
@@ -246,15 +268,15 @@ void cut_and_weights(gp_ctx *ctx, const DevGraph &g, const int32_t *blocks, int3
   DBuf<unsigned long long> c(ctx, 1);
   c.zero();
   if (g.m2 > 0) {
-    const int grid = grid_for((g.m2 + 1023) / 1024 * 32, 256, ctx->num_sms * 16);
+    const int grid = grid_for(g.n, 256, ctx->num_sms * 16);
     if (k <= 255) {
       DBuf<uint8_t> b8(ctx, (size_t)g.n);
       k_narrow<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(blocks, g.n, b8.get());
       GP_LAUNCH_CHECK();
-      k_cut<uint8_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, b8.get(), g.n, g.m2, c.get());
+      k_cut<uint8_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, b8.get(), g.n, c.get());
       GP_LAUNCH_CHECK();
     } else {
-      k_cut<int32_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, blocks, g.n, g.m2, c.get());
+      k_cut<int32_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, blocks, g.n, c.get());
       GP_LAUNCH_CHECK();
     }
   }

@@ -158,6 +158,7 @@ gp_status gp_server_create(gp_server **out, int device, int32_t workers, int64_t
       gp_server_destroy(s);
       return GP_ERR_CUDA;
     }
+    c->device_share = workers;
     s->ctxs.push_back(c);
     s->streams.push_back(st);
   }
