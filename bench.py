@@ -397,6 +397,11 @@ def run_gpu(args, world, rank, local):
 
     if rank != 0:
         return 0
+    # the batched and served forms on bounded samples of their mixes (one GPU only)
+    batched = served = None
+    if world == 1 and not args.no_batch_serve:
+        batched = batch_summary(gp, args.batch_count, args.batch_nmax, args.batch_workers, 1, 1)
+        served = serve_summary(gp, args.serve_count, args.serve_mmax, args.serve_workers)
     cb = None
     if not args.no_cpu_baseline:
         m_s, times = cpu_sample_run(1)
@@ -416,6 +421,7 @@ def run_gpu(args, world, rank, local):
             "rebalance_moves": st.rebalance_moves, "n_coarsest": st.n_coarsest,
             "hierarchy": {"columns": ["n", "m", "n_next", "m_coarse", "m_hat", "triggered", "m_next"],
                           "levels": hierarchy},
+            "batched": batched, "served": served,
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches // max(args.steps, 1),
             "gpu_launches_total": launches, "clocks": clk, "modularity_level1": mod,
             "kernel_classes_from": "a second pass over the same steps with per-class CUDA events "
@@ -497,44 +503,48 @@ def batch_mix(count, nmax, seed):
     return jobs
 
 
-def run_batch(args):
+def batch_summary(gp, count, nmax, workers, warmup, steps):
     """Batched form: the same graphs one gp_partition call after another, then all at once through
-    gp_partition_batch; graphs/s of both, and the results must agree item by item."""
-    import numpy as np
+    gp_partition_batch; graphs/s of both (best of `steps` passes after `warmup`), and whether the
+    results agree item by item."""
     import torch
-    import paper_2504_17615_gb300 as gp
-    from paper_2504_17615_gb300 import build as gpbuild
-    gpbuild.build()
     t = time.time()
-    jobs = batch_mix(args.batch_count, args.batch_nmax, 1)
+    jobs = batch_mix(count, nmax, 1)
     log(f"[bench] generated {len(jobs)} graphs in {time.time() - t:.1f}s")
     ctx = gp.Context(0)
     dev = [(gp.DeviceGraph.from_host(g), k, e, sd) for g, k, e, sd in jobs]
     torch.cuda.synchronize()
     serial = batched = None
-    for rep in range(args.warmup + args.steps):
+    for rep in range(warmup + steps):
         t = time.perf_counter()
         ser = [ctx.gp_partition(dg, k, e, sd)[:2] for dg, k, e, sd in dev]
         torch.cuda.synchronize()
         ts = time.perf_counter() - t
         t = time.perf_counter()
-        bat = ctx.gp_partition_batch(dev, workers=args.batch_workers)
+        bat = ctx.gp_partition_batch(dev, workers=workers)
         torch.cuda.synchronize()
         tb = time.perf_counter() - t
-        if rep >= args.warmup:
+        if rep >= warmup:
             serial = ts if serial is None else min(serial, ts)
             batched = tb if batched is None else min(batched, tb)
     same = all(c1 == c2 and torch.equal(b1, b2) for (b1, c1), (b2, c2) in zip(ser, bat))
-    edges = sum(g.m for g, _, _, _ in jobs)
-    print(json.dumps({"metric": "batched graphs/s", "value": len(jobs) / batched, "unit": "graphs/s",
-                      "serial_graphs_per_s": len(jobs) / serial, "speedup": serial / batched,
-                      "identical_results": same, "graphs": len(jobs), "edges": edges,
-                      "workers": args.batch_workers, "steps": args.steps, "warmup": args.warmup,
-                      "timing": "best of the timed repetitions, host wall clock around each pass",
-                      "config": {"workload": f"{len(jobs)} graphs, n log-uniform in [1e3, {args.batch_nmax:g}], "
-                                             "ER deg 8-32 / 2D grid / 3D grid / R-MAT ef 8, k in {2..64}, eps 0.03"}}),
-          flush=True)
     ctx.close()
+    return {"graphs_per_s": len(jobs) / batched, "serial_graphs_per_s": len(jobs) / serial,
+            "speedup": serial / batched, "identical_results": same, "graphs": len(jobs),
+            "edges": sum(g.m for g, _, _, _ in jobs), "workers": workers,
+            "timing": f"best of {steps} pass(es) after {warmup}, host wall clock around each pass",
+            "workload": f"{len(jobs)} graphs, n log-uniform in [1e3, {nmax:g}], ER deg 8-32 / 2D grid / 3D grid / "
+                        "R-MAT ef 8, k in {2..64}, eps 0.03 (C4 mix)"}
+
+
+def run_batch(args):
+    import paper_2504_17615_gb300 as gp
+    from paper_2504_17615_gb300 import build as gpbuild
+    gpbuild.build()
+    out = batch_summary(gp, args.batch_count, args.batch_nmax, args.batch_workers, args.warmup, args.steps)
+    out.update({"metric": "batched graphs/s", "value": out["graphs_per_s"], "unit": "graphs/s",
+                "steps": args.steps, "warmup": args.warmup, "config": {"workload": out["workload"]}})
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -594,38 +604,48 @@ def serve_run(gp, reqs, arrivals, workers, budget):
     return lat, wall, res
 
 
-def run_serve(args):
-    """Served form: a Poisson stream of requests through the library's request loop, 8 workers
-    against 1 worker (the plain one-request-at-a-time path) on the same arrival times."""
+def serve_summary(gp, count, mmax, workers):
+    """Served form: a Poisson stream of requests through the library's request loop.  The
+    capacity with `workers` workers is measured closed-loop (all requests at once); then Poisson
+    arrivals at 70% of it (sustained load) and at 150% of it (saturated), each served with `workers`
+    workers and with one worker (the plain one-request-at-a-time path) on the same arrivals."""
     import numpy as np
-    import torch
+    t = time.time()
+    reqs = serve_mix(count, mmax, 2)
+    log(f"[bench] generated {len(reqs)} requests in {time.time() - t:.1f}s")
+    budget = 96 << 30
+    _, closed1, _ = serve_run(gp, reqs, [0.0] * len(reqs), 1, budget)
+    _, closedw, _ = serve_run(gp, reqs, [0.0] * len(reqs), workers, budget)
+    out = {"requests": len(reqs), "edges": sum(r[0].m for r in reqs), "hbm_budget_bytes": budget,
+           "capacity_graphs_per_s": {"workers_1": len(reqs) / closed1, f"workers_{workers}": len(reqs) / closedw},
+           "workload": f"{len(reqs)} requests, m log-uniform in [1e4, {mmax:g}], ER / 2D grid / 3D grid / R-MAT, "
+                       "k in {2, 8, 32, 128}, eps 0.03, Poisson arrivals (C5 mix)"}
+    same = True
+    for name, lam in (("sustained", 0.7 * len(reqs) / closedw), ("saturated", 1.5 * len(reqs) / closedw)):
+        arrivals = np.cumsum(np.random.default_rng(3).exponential(1.0 / lam, len(reqs))).tolist()
+        rec = {"arrival_rate_per_s": lam}
+        res = {}
+        for w in (1, workers):
+            lat, wall, r = serve_run(gp, reqs, arrivals, w, budget)
+            res[w] = r
+            rec[f"workers_{w}"] = {"graphs_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                                   "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(np.mean(lat))}
+            log(f"[bench] serve {name} workers={w}: {len(reqs) / wall:.1f} graphs/s p50 "
+                f"{rec[f'workers_{w}']['p50_ms']:.1f} ms p99 {rec[f'workers_{w}']['p99_ms']:.1f} ms")
+        same = same and all(c1 == c2 and np.array_equal(b1, b2) for (b1, c1), (b2, c2) in zip(res[1], res[workers]))
+        out[name] = rec
+    out["identical_results"] = same
+    return out
+
+
+def run_serve(args):
     import paper_2504_17615_gb300 as gp
     from paper_2504_17615_gb300 import build as gpbuild
     gpbuild.build()
-    t = time.time()
-    reqs = serve_mix(args.serve_count, args.serve_mmax, 2)
-    log(f"[bench] generated {len(reqs)} requests in {time.time() - t:.1f}s")
-    budget = 96 << 30
-    # the one-worker path's service rate fixes the arrival rate: twice what it can serve
-    _, closed, _ = serve_run(gp, reqs, [0.0] * len(reqs), 1, budget)
-    lam = 2.0 * len(reqs) / closed
-    arrivals = np.cumsum(np.random.default_rng(3).exponential(1.0 / lam, len(reqs))).tolist()
-    out = {"metric": "served graphs/s and p50/p99 latency", "arrival_rate_per_s": lam,
-           "requests": len(reqs), "edges": sum(r[0].m for r in reqs), "hbm_budget_bytes": budget,
-           "config": {"workload": f"{len(reqs)} requests, m log-uniform in [1e4, {args.serve_mmax:g}], "
-                                  "ER / 2D grid / 3D grid / R-MAT, k in {2, 8, 32, 128}, eps 0.03, Poisson arrivals"}}
-    results = {}
-    for w in (1, args.serve_workers):
-        lat, wall, res = serve_run(gp, reqs, arrivals, w, budget)
-        results[w] = res
-        out[f"workers_{w}"] = {"graphs_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50)),
-                               "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(np.mean(lat))}
-        log(f"[bench] serve workers={w}: {len(reqs) / wall:.1f} graphs/s p50 {out[f'workers_{w}']['p50_ms']:.1f} ms "
-            f"p99 {out[f'workers_{w}']['p99_ms']:.1f} ms")
-    out["identical_results"] = all(c1 == c2 and np.array_equal(b1, b2)
-                                   for (b1, c1), (b2, c2) in zip(results[1], results[args.serve_workers]))
-    out["value"] = out[f"workers_{args.serve_workers}"]["graphs_per_s"]
-    out["unit"] = "graphs/s"
+    out = serve_summary(gp, args.serve_count, args.serve_mmax, args.serve_workers)
+    out.update({"metric": "served graphs/s and p50/p99 latency",
+                "value": out["sustained"][f"workers_{args.serve_workers}"]["graphs_per_s"], "unit": "graphs/s",
+                "config": {"workload": out["workload"]}})
     print(json.dumps(out), flush=True)
     return 0
 
@@ -672,6 +692,8 @@ def main():
                     help="ER graph with 2^S nodes and average degree 20 instead (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch-serve", action="store_true",
+                    help="leave the batched and served summaries out of the default line")
     ap.add_argument("--batch", action="store_true",
                     help="batched form: many independent graphs, serial calls against gp_partition_batch")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -680,7 +702,7 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="served form: Poisson request stream through the request loop, p50/p99 latency")
     ap.add_argument("--serve-count", type=int, default=128)
-    ap.add_argument("--serve-mmax", type=float, default=3e6)
+    ap.add_argument("--serve-mmax", type=float, default=1e8)
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--report", action="store_true",
                     help="per-level hierarchy of the workload with each sparsifier (no timing contract)")

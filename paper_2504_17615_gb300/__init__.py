@@ -293,7 +293,8 @@ class Context:
     library's own stream-ordered pool, or from torch's caching allocator when
     use_torch_allocator is set (one Python call per allocation: slower)."""
 
-    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = False):
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = False,
+                 allocator: "gp_allocator | None" = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device available: the partitioner runs on the GPU only")
@@ -319,6 +320,9 @@ class Context:
                     pass
 
             alloc = gp_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+            self._keep.append(alloc)
+        if allocator is not None:  # a caller's gp_allocator (its callbacks must outlive the context)
+            alloc = allocator
             self._keep.append(alloc)
         p = ctypes.c_void_p()
         st = self.lib.gp_create(ctypes.byref(p), device, ctypes.c_void_p(self.stream.cuda_stream),

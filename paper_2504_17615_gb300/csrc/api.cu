@@ -136,6 +136,10 @@ void gp_destroy(gp_ctx *ctx) {
     cudaEventDestroy(r.b);
   }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
+  for (auto st : ctx->copy_streams)
+    if (st) cudaStreamDestroy(st);
+  for (auto ev : ctx->copy_events)
+    if (ev) cudaEventDestroy(ev);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->d_units) cudaFree(ctx->d_units);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // released once its last allocation is freed
@@ -213,13 +217,10 @@ gp_status gp_partition_host(gp_ctx *ctx, int32_t n, int64_t m2, const int32_t *x
     gp::DevGraph d;
     d.allocate(ctx, n, m2);
     gp::DBuf<int32_t> b(ctx, (size_t)n);
-    GP_CUDA(cudaMemcpyAsync(d.xadj, xadj, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, ctx->stream));
-    if (m2 > 0) {
-      GP_CUDA(cudaMemcpyAsync(d.adjncy, adjncy, sizeof(int32_t) * m2, cudaMemcpyHostToDevice, ctx->stream));
-      GP_CUDA(cudaMemcpyAsync(d.adjwgt, adjwgt, sizeof(int32_t) * m2, cudaMemcpyHostToDevice, ctx->stream));
-    }
-    if (n > 0)
-      GP_CUDA(cudaMemcpyAsync(d.vwgt, vwgt, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+    gp::copy_to_device(ctx, {{d.xadj, xadj, sizeof(int32_t) * ((size_t)n + 1)},
+                             {d.adjncy, adjncy, sizeof(int32_t) * (size_t)m2},
+                             {d.adjwgt, adjwgt, sizeof(int32_t) * (size_t)m2},
+                             {d.vwgt, vwgt, sizeof(int32_t) * (size_t)n}});
     gp::partition_impl(ctx, d, k, eps, seed, c, b.get(), cut, stats);
     if (n > 0) GP_CUDA(cudaMemcpyAsync(blocks, b.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
     GP_CUDA(cudaStreamSynchronize(ctx->stream));

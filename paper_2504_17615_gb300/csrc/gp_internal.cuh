@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -114,6 +115,8 @@ struct gp_ctx {
   std::vector<gp_ctx *> workers;                 // batch workers (own streams and pools)
   int64_t wait_spins = 0;                        // limit of device-side waits (0: default)
   int device_share = 1;  // contexts sharing the device (batch / server workers): persistent grids shrink
+  cudaStream_t copy_streams[4] = {};  // host-to-device copies of large inputs
+  cudaEvent_t copy_events[5] = {};
 };
 
 namespace gp {
@@ -161,6 +164,14 @@ struct DBuf {
     if (p) GP_CUDA(cudaMemsetAsync(p, byte, (count ? count : 1) * sizeof(T), ctx->stream));
   }
 };
+
+// One host-to-device copy of copy_to_device.
+struct HostCopy {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+void copy_to_device(gp_ctx *ctx, std::initializer_list<HostCopy> parts);
 
 // Copies `n` device int64 values to the host (synchronises the stream).
 void read_back(gp_ctx *ctx, const void *dev, size_t bytes, void *host);

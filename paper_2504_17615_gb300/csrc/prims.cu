@@ -41,6 +41,43 @@ void read_back(gp_ctx *ctx, const void *dev, size_t bytes, void *host) {
   }
 }
 
+// Host-to-device copies of large arrays: 256 MiB chunks spread round-robin
+// over four streams of the context (several copy engines in flight), ordered
+// after the context stream's earlier work and joined back into it.
+void copy_to_device(gp_ctx *ctx, std::initializer_list<HostCopy> parts) {
+  constexpr size_t kChunk = (size_t)256 << 20;
+  constexpr int kStreams = 4;
+  size_t total = 0;
+  for (const HostCopy &h : parts) total += h.bytes;
+  if (total <= kChunk) {
+    for (const HostCopy &h : parts)
+      if (h.bytes) GP_CUDA(cudaMemcpyAsync(h.dst, h.src, h.bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return;
+  }
+  if (!ctx->copy_streams[0]) {
+    for (int i = 0; i < kStreams; i++) {
+      GP_CUDA(cudaStreamCreateWithFlags(&ctx->copy_streams[i], cudaStreamNonBlocking));
+      GP_CUDA(cudaEventCreateWithFlags(&ctx->copy_events[i], cudaEventDisableTiming));
+    }
+    GP_CUDA(cudaEventCreateWithFlags(&ctx->copy_events[kStreams], cudaEventDisableTiming));
+  }
+  GP_CUDA(cudaEventRecord(ctx->copy_events[kStreams], ctx->stream));
+  for (int i = 0; i < kStreams; i++) GP_CUDA(cudaStreamWaitEvent(ctx->copy_streams[i], ctx->copy_events[kStreams], 0));
+  int next = 0;
+  for (const HostCopy &h : parts) {
+    for (size_t off = 0; off < h.bytes; off += kChunk) {
+      const size_t len = h.bytes - off < kChunk ? h.bytes - off : kChunk;
+      GP_CUDA(cudaMemcpyAsync(static_cast<char *>(h.dst) + off, static_cast<const char *>(h.src) + off, len,
+                              cudaMemcpyHostToDevice, ctx->copy_streams[next]));
+      next = (next + 1) % kStreams;
+    }
+  }
+  for (int i = 0; i < kStreams; i++) {
+    GP_CUDA(cudaEventRecord(ctx->copy_events[i], ctx->copy_streams[i]));
+    GP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->copy_events[i], 0));
+  }
+}
+
 // --------------------------------------------------------------- profiling
 
 static cudaEvent_t take_event(gp_ctx *ctx) {

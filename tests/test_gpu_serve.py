@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle as orc
 
 pytestmark = pytest.mark.gpu
 
@@ -74,11 +75,20 @@ def test_results_equal_alone_and_in_the_mix(gp, ctx):
         th = threading.Thread(target=lambda: late.extend(srv.submit(*r) for r in reqs[16:]))
         th.start()
         th.join()
+        served = []
         for i, t in enumerate(tickets + late):
             blocks, cut, resp = srv.wait(t)
             assert resp.status == gp.GP_OK
             assert cut == ref[i][1] and np.array_equal(blocks, ref[i][0]), f"request {i}"
             assert resp.total_ms >= resp.run_ms >= 0.0
+            served.append((blocks.copy(), cut))
+        # the smallest requests, served in the mix, against the CPU oracle
+        small = sorted(range(len(reqs)), key=lambda i: reqs[i][0].m)[:4]
+        for i in small:
+            g, k, eps, seed = reqs[i]
+            r = orc.partition(g, k, eps, seed)
+            assert r.rc == orc.OK
+            assert served[i][1] == r.cut and np.array_equal(served[i][0], r.blocks), f"request {i} vs oracle"
     finally:
         srv.close()
 
