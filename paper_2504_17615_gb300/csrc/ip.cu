@@ -16,10 +16,18 @@
 // A node costs O(deg + n'/64), not O(n'): node lists are sorted by id, so
 // local index order is id order; every 64-node chunk keeps the largest key
 // (gain, -index) of its live frontier nodes, raised with a 64-bit atomicMax
-// when a neighbour's connection grows and recomputed only for the chunk of
-// the node just taken.  A picked node that no longer fits is retired for
+// when a neighbour's connection grows and recomputed only for the chunks of
+// the nodes just taken.  A picked node that no longer fits is retired for
 // good (side 1 only gets heavier), which leaves the choice among the nodes
 // that fit unchanged.
+//
+// Steps of B >= 8 nodes select their nodes together instead of one by one:
+// the chunk maxima are sorted, the q-th largest of them (q = nodes still
+// wanted) is a threshold that at least q frontier nodes reach, and all of
+// those lie in the q leading chunks; they are ranked, and one warp walks them
+// in key order with prefix sums of their weights, taking, retiring or
+// stopping exactly as the one-by-one walk would.  A round that runs out of
+// candidates (retired nodes) selects again.
 #include "gp_internal.cuh"
 
 #include <algorithm>
@@ -30,7 +38,11 @@ namespace {
 
 constexpr int kUpdUnroll = 4;
 constexpr int kChunkNodes = 64;
-constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // dynamic part (static shared variables use the rest)
+constexpr int kBatchMinB = 8;    // steps of at least this many nodes select them together
+constexpr int kSortCap = 512;    // chunk maxima sorted per selection round
+constexpr int kCandCap = 256;    // candidates ranked per round; more fall back to one-by-one extraction
+// dynamic part (static shared variables use the rest: the sort and candidate buffers and a few words)
+constexpr int kMaxSmemBytes = 227 * 1024 - (kSortCap + 2 * kCandCap) * 8 - 1024;
 
 struct Sub {
   int32_t start, count;  // node list range
@@ -104,15 +116,35 @@ __device__ __forceinline__ void rescan_chunk(int c, int cnt, const int32_t *g, c
 
 constexpr int kIpWarps = 4;  // warps per (subproblem, trial)
 
+// Sorts x[0, P) into descending order (P a power of two); all threads of the
+// block take part, and the block is synchronised on return.
+__device__ __forceinline__ void bitonic_desc(unsigned long long *x, int P) {
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+        const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+        const bool desc = (i & size) == 0;
+        const unsigned long long u = x[i], w = x[j];
+        if ((u < w) == desc) { x[i] = w; x[j] = u; }
+      }
+      __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int node_of(unsigned long long key) {
+  return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+}
+
 // One block of kIpWarps warps per (subproblem, trial).  Warp 0 takes the
 // step's nodes from the chunk tournament; all warps then raise the
 // connections of the taken nodes' neighbours, scan for the fallback node and
 // add up the trial's cut.
 __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
   extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ int s_nb;
+  __shared__ int s_nb, s_nz, s_nc;
   __shared__ long long s_w1;
   __shared__ unsigned long long s_red[kIpWarps];
+  __shared__ unsigned long long s_sort[kSortCap], s_cand[kCandCap], s_rank[kCandCap];
   const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
   const int si = blockIdx.x / a.trials, t = blockIdx.x % a.trials;
   const Sub S = a.subs[si];
@@ -150,14 +182,121 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
   int64_t w1 = 0;  // warp 0's copy is the authoritative one; others read s_w1
   const int B = 1 + cnt / 1024;  // nodes per growing step
   int32_t *batch = a.gbatch + (int64_t)blockIdx.x * a.batch_cap;
+  const bool batched = B >= kBatchMinB && cnt <= a.smem_nodes && nch <= kSortCap;
+  int P = 64;
+  while (P < nch) P <<= 1;
   for (;;) {
     if (threadIdx.x == 0) s_w1 = w1;
     __syncthreads();
     w1 = s_w1;
     if (w1 >= S.T1) break;
-    // warp 0: up to B nodes in (gain desc, id asc) order; gains stay frozen until the step ends
-    if (warp == 0) {
-      int nb = 0;
+    // up to B nodes in (gain desc, id asc) order; gains stay frozen until the step ends
+    bool seq = !batched;
+    if (batched) {
+      if (threadIdx.x == 0) {
+        s_nb = 0;
+        if (a.trace) atomicAdd(a.trace + 0, 1ull);
+      }
+      for (;;) {  // selection rounds
+        __syncthreads();
+        const int nb0 = s_nb;
+        const long long w10 = s_w1;
+        if (nb0 >= B || w10 >= S.T1) break;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) s_sort[i] = i < nch ? best[i] : 0ull;
+        if (threadIdx.x == 0) { s_nz = 0; s_nc = 0; }
+        __syncthreads();
+        bitonic_desc(s_sort, P);
+        for (int i = threadIdx.x; i < P; i += blockDim.x)
+          if (s_sort[i] != 0 && (i + 1 == P || s_sort[i + 1] == 0)) s_nz = i + 1;
+        __syncthreads();
+        const int nz = s_nz;
+        if (nz == 0) break;  // no frontier node left
+        const int q = min(B - nb0, nz);
+        const unsigned long long tau = s_sort[q - 1];
+        // every frontier node with key >= tau sits in one of the q leading chunks
+        for (int r = warp; r < q; r += kIpWarps) {
+          const int c = node_of(s_sort[r]) / kChunkNodes;
+#pragma unroll
+          for (int rr = 0; rr < kChunkNodes / 32; rr++) {
+            const int j = c * kChunkNodes + rr * 32 + lane;
+            unsigned long long key = 0;
+            if (j < cnt && st[j] == S_FRONT) key = gain_key(g[j], j);
+            const bool is = key >= tau && key != 0;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, is);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&s_nc, __popc(m));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            const int pos = base + __popc(m & lanemask_lt());
+            if (is && pos < kCandCap) s_cand[pos] = key;
+          }
+        }
+        __syncthreads();
+        const int C = s_nc;
+        if (C > kCandCap) { seq = true; break; }
+        for (int i = threadIdx.x; i < C; i += blockDim.x) {  // keys are distinct: rank = place
+          const unsigned long long x = s_cand[i];
+          int r = 0;
+          for (int i2 = 0; i2 < C; i2++) r += s_cand[i2] > x ? 1 : 0;
+          s_rank[r] = x;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          int nb = nb0;
+          long long w = w10;
+          int i0 = 0;
+          while (i0 < C) {
+            const int i = i0 + lane;
+            int j = -1;
+            long long c = 0;
+            if (i < C) {
+              j = node_of(s_rank[i]);
+              c = cv ? (long long)cv[j] : (long long)a.cvl[start + j];
+            }
+            long long pre = c;  // weight of lanes i0..i
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const long long y = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+              if (lane >= o) pre += y;
+            }
+            // lane i is reached iff every earlier lane of the group was taken
+            const bool considered = i < C && nb + (i - i0) < B && w + (pre - c) < S.T1;
+            const bool fits = w + pre <= S.L1;
+            const unsigned bad = __ballot_sync(0xFFFFFFFFu, !(considered && fits));
+            const int f = bad ? __ffs(bad) - 1 : 32;
+            if (lane < f) {
+              st[j] = S_ONE;
+              batch[nb + lane] = j;
+            }
+            const long long wf = __shfl_sync(0xFFFFFFFFu, pre, f > 0 ? f - 1 : 0);
+            const bool cf = __shfl_sync(0xFFFFFFFFu, considered, f < 32 ? f : 0);
+            if (f > 0) w += wf;
+            nb += f;
+            if (f == 32) { i0 += 32; continue; }
+            if (i0 + f >= C || !cf) break;  // list used up, or the step is complete
+            if (lane == f) {  // reached and does not fit: retired
+              st[j] = S_OUT;
+              if (a.trace) atomicAdd(a.trace + 2, 1ull);
+            }
+            i0 += f + 1;
+          }
+          if (lane == 0) { s_nb = nb; s_w1 = w; }
+        }
+        __syncthreads();
+        for (int r = warp; r < q; r += kIpWarps) rescan_chunk(node_of(s_sort[r]) / kChunkNodes, cnt, g, st, best);
+      }
+      __syncthreads();
+      if (seq) {  // the chunk groups' maxima again for the one-by-one walk
+        for (int sc = warp; sc < nsup; sc += kIpWarps) {
+          const int c = sc * 32 + lane;
+          const unsigned long long x = wmax_u64(c < nch ? best[c] : 0ull);
+          if (lane == 0) sup[sc] = x;
+        }
+        __syncthreads();
+        w1 = s_w1;
+      }
+    }
+    if (seq && warp == 0) {
+      int nb = batched ? s_nb : 0;
       while (nb < B && w1 < S.T1) {
         unsigned long long b = 0;
         for (int c = lane; c < nsup; c += 32) b = sup[c] > b ? sup[c] : b;
@@ -184,7 +323,7 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
       if (lane == 0) {
         s_nb = nb;
         s_w1 = w1;
-        if (a.trace) atomicAdd(a.trace + 0, 1ull);
+        if (a.trace && !batched) atomicAdd(a.trace + 0, 1ull);
       }
     }
     __syncthreads();

@@ -29,12 +29,14 @@ struct GroupTable {
 // together (gmask: the caller's group); tk / tv: the group's TS slots, empty
 // (-1 / 0) on entry and left empty.  label8 (may be null) replaces label for
 // the gathers.  weight: global label weights (unused with s_wl or FAV).
+// stable: no label other than own is rated above own, admissible or not, so
+// the node cannot propose until a neighbour's label changes (not FAV).
 template <int G, int E, bool FAV>
 __device__ __forceinline__ unsigned rate_group(const int32_t *__restrict__ adjncy, const int32_t *__restrict__ adjwgt,
                                                const int32_t *label, const uint8_t *label8, const int32_t *weight,
                                                const int *s_wl, int64_t bound, uint64_t ktie, int v, int st,
                                                int deg, int own, int cv, int *tk, int *tv, unsigned gmask, int gl,
-                                               bool stream_rows, int &ncand) {
+                                               bool stream_rows, int &ncand, bool &stable) {
   constexpr int TS = GroupTable<G, E>::TS;
   constexpr int BITS = GroupTable<G, E>::BITS;
   int L[E], w[E], slot[E], sum[E];
@@ -83,6 +85,14 @@ __device__ __forceinline__ unsigned rate_group(const int32_t *__restrict__ adjnc
   for (int e = 0; e < E; e++)
     if (lead[e]) { tk[slot[e]] = -1; tv[slot[e]] = 0; }
   const int own_r = FAV ? -1 : (int)__reduce_max_sync(gmask, own_loc);
+  stable = false;
+  if (!FAV) {
+    unsigned rl_all = 0;
+#pragma unroll
+    for (int e = 0; e < E; e++)
+      if (lead[e] && L[e] != own) rl_all = max(rl_all, (unsigned)sum[e]);
+    stable = (int)__reduce_max_sync(gmask, rl_all) <= own_r;
+  }
   bool alive[E];
   ncand = 0;
 #pragma unroll

@@ -27,6 +27,11 @@
 //           the weight transitions (a cluster weight reaching zero or leaving
 //           zero), every transition an atomic, so the count is exact
 //
+// Refinement skips nodes that cannot move: a node whose rating found no label
+// rated above its own (admissible or not) proposes nothing until a neighbour
+// changes its label, so it is not rated again until a move of a neighbour (or
+// its own) marks it; the result is unchanged.
+//
 // Every grid barrier waits with an iteration limit; when it runs out the
 // kernel records GP_ERR_TIMEOUT in a status word and every block returns.
 #include "lp.cuh"
@@ -78,6 +83,7 @@ struct PArgs {
   int n;
   int32_t *label, *weight;
   uint8_t *label8;
+  uint8_t *dirty;        // refinement: per node, 0 = cannot move until a neighbour moves (may be null)
   int64_t nlabels;
   int64_t bound, n_min;
   int count_clusters, rounds, S, dbg_max, level;
@@ -181,22 +187,25 @@ __device__ __forceinline__ void propose(const PArgs &a, PCount *c, int v, int K,
 // `lane` with stride `step`: own rating, then the admissible label of largest
 // rating, ties by the smallest h32(ktie, v, L), then the smallest label.
 // Returns the packed (hash << 32 | label) of the best candidate, ~0 if none,
-// via the reductions red_max / red_min.
+// via the reductions red_max / red_min; stable: no label other than own rated
+// above own (computed only when the skip flags are kept).
 template <typename RMAX, typename RMIN>
 __device__ __forceinline__ uint64_t choose(const PArgs &a, const int *tk, const int *tv, int size, int tid,
                                            int step, int v, int own, int cv, uint64_t ktie, RMAX red_max,
-                                           RMIN red_min, int &own_r_out, int &rmax_out) {
-  int own_loc = 0, rloc = -1;
+                                           RMIN red_min, int &own_r_out, int &rmax_out, bool &stable) {
+  int own_loc = 0, rloc = -1, rall = 0;
   for (int t = tid; t < size; t += step) {
     const int L = tk[t];
     if (L < 0) continue;
     const int r = tv[t];
     if (L == own) { own_loc = r; continue; }
+    rall = r > rall ? r : rall;
     if ((int64_t)a.weight[L] + cv > a.bound) continue;
     rloc = r > rloc ? r : rloc;
   }
   const int own_r = red_max(own_loc);
   const int rmax = red_max(rloc);
+  stable = a.dirty != nullptr && red_max(rall) <= own_r;
   own_r_out = own_r;
   rmax_out = rmax;
   if (rmax < 0 || rmax <= own_r) return ~0ull;
@@ -291,7 +300,8 @@ __device__ __forceinline__ void rate_list(const PArgs &a, PCount *c, const int32
   const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
   for (int i0 = gw * NV; i0 < count; i0 += nw * NV) {
     const int i = i0 + grp;
-    const int v = i < count ? list[i] : -1;
+    int v = i < count ? list[i] : -1;
+    if (v >= 0 && a.dirty && !a.dirty[v]) v = -1;  // cannot move until a neighbour moves
     int st = 0, deg = 0, own = -2, cv = 0;
     if (v >= 0) {
       st = a.xadj[v];
@@ -300,13 +310,15 @@ __device__ __forceinline__ void rate_list(const PArgs &a, PCount *c, const int32
       cv = a.vwgt[v];
     }
     int nc = 0;
+    bool stable = false;
     const unsigned best = rate_group<G, E, false>(a.adjncy, a.adjwgt, a.label, a.label8, a.weight, s_wl, a.bound,
                                                   ktie, v, st, deg, own, cv, tk + grp * TS, tv + grp * TS, gmask,
-                                                  gl, false, nc);
+                                                  gl, false, nc, stable);
     if (gl == 0 && v >= 0) {
       ue += deg;
       uv += 1;
       if (best != 0xFFFFFFFFu) propose(a, c, v, (int)best, own, cv);
+      if (a.dirty && stable) a.dirty[v] = 0;
     }
   }
 }
@@ -446,6 +458,8 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
         }
         for (int h = h0 + blockIdx.x; h < h1 && (int)blockIdx.x < a.hblocks; h += a.hblocks) {
           const int v = a.blist[h];
+          // read by every thread before thread 0 may clear it below (barriers in between)
+          if (a.dirty && !a.dirty[v]) continue;
           const int st = a.xadj[v], deg = a.xadj[v + 1] - st;
           int bits = 1;
           while ((1 << bits) < 2 * deg) bits++;
@@ -466,13 +480,15 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
           }
           __syncthreads();
           int own_r, rmax;
+          bool stable;
           const uint64_t best = choose(a, k2, v2, tsize, threadIdx.x, blockDim.x, v, own, cv, ktie,
                                        [&](int x) { return block_max_int(x, s_ri); },
-                                       [&](uint64_t x) { return block_min_u64(x, s_ru); }, own_r, rmax);
+                                       [&](uint64_t x) { return block_min_u64(x, s_ru); }, own_r, rmax, stable);
           if (threadIdx.x == 0) {
             ue += deg;
             uv += 1;
             if (best != ~0ull) propose(a, c, v, (int)(uint32_t)best, own, cv);
+            if (stable) a.dirty[v] = 0;
           }
           __syncthreads();
           for (int t = threadIdx.x; t < tsize; t += blockDim.x) { k2[t] = -1; v2[t] = 0; }
@@ -745,6 +761,16 @@ __global__ void __launch_bounds__(kPThreads) k_lp_persistent(PArgs a) {
         for (int q = threadIdx.x; q < (int)a.nlabels; q += blockDim.x)
           if (s_dw[q]) atomicAdd(&a.weight[q], s_dw[q]);
       }
+      if (a.dirty) {  // every applied move marks its node and the node's neighbours, a warp per move
+        for (int i = gw; i < nprop; i += nw) {
+          if (!a.acc[i]) continue;
+          const int v = a.prop[i].x;
+          if (cutoff != ~0ull && pkey(kprio, v) >= cutoff) continue;
+          const int e0 = a.xadj[v], e1 = a.xadj[v + 1];
+          if (lane == 0) a.dirty[v] = 1;
+          for (int e = e0 + lane; e < e1; e += 32) a.dirty[a.adjncy[e]] = 1;
+        }
+      }
       moved = warp_sum(moved);
       delta = warp_sum(delta);
       if (lane == 0) {
@@ -858,6 +884,11 @@ LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *w
     dkey.zero();
   }
   incoming.zero();
+  DBuf<uint8_t> dirty;
+  if (!p.count_clusters) {
+    dirty.reset(ctx, (size_t)n);
+    dirty.fill_bytes(1);
+  }
   // global rating tables for nodes whose table exceeds the shared one
   DBuf<int> md(ctx, 1);
   md.zero();
@@ -891,6 +922,7 @@ LpResult lp_run_small(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *w
   PArgs a{};
   a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt; a.n = n;
   a.label = label; a.weight = weight; a.label8 = label8; a.nlabels = nlabels;
+  a.dirty = p.count_clusters ? nullptr : dirty.get();
   a.bound = p.bound; a.n_min = p.n_min; a.count_clusters = p.count_clusters ? 1 : 0;
   a.rounds = p.rounds; a.S = p.subrounds; a.dbg_max = p.dbg_max_subrounds; a.level = p.level;
   a.seed = seed; a.tag_act = p.tag_act; a.tag_tie = p.tag_tie; a.tag_prio = p.tag_prio;

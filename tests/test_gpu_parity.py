@@ -204,11 +204,29 @@ def test_initial_partition_matches_oracle(gp, ctx, k):
 
 
 def test_initial_partition_large_subproblem_uses_global_state(gp, ctx):
-    g = gg.er(14000, 40000, 8)   # above the shared-memory node limit
+    g = gg.er(45000, 130000, 8)   # above the shared-memory node limit (about 31k nodes)
     dg = gp.DeviceGraph.from_host(g)
     blk = ctx.gp_initial_partition(dg, 2, 0.03, 2, gp.default_config(ip_trials=2))
     oblk = orc.initial_partition(g, 2, 30000, 2, trials=2)
     assert np.array_equal(blk.cpu().numpy(), oblk)
+
+
+@pytest.mark.parametrize("name", ["er", "er_heavy", "grid", "star", "rmat"])
+def test_initial_partition_steps_of_many_nodes_match_oracle(gp, ctx, name):
+    """Subproblems of 8k-30k nodes (growing steps of B = 8..30 nodes, selected together): plain
+    ER; ER with node weights up to 5000 (nodes that no longer fit are retired mid-step); a grid
+    (many equal gains); a star (after the centre every leaf has the same gain, so the candidates
+    overflow the ranked set and the step falls back to one-by-one extraction); R-MAT."""
+    g = {"er": lambda: gg.er(20000, 90000, 21),
+         "er_heavy": lambda: gg.with_node_weights(gg.er(16000, 70000, 22), 5000),
+         "grid": lambda: gg.grid2d(110, 100),
+         "star": lambda: star(10000),
+         "rmat": lambda: gg.rmat(14, 6, seed=23)}[name]()
+    dg = gp.DeviceGraph.from_host(g)
+    for k, trials in ((2, 3), (5, 2)):
+        blk = ctx.gp_initial_partition(dg, k, 0.03, 9, gp.default_config(ip_trials=trials))
+        oblk = orc.initial_partition(g, k, 30000, 9, trials=trials)
+        assert np.array_equal(blk.cpu().numpy(), oblk), (name, k)
 
 
 @pytest.mark.parametrize("k", [2, 5, 8])
