@@ -36,13 +36,15 @@ namespace gp {
 
 namespace {
 
-constexpr int kUpdUnroll = 4;
+constexpr int kUpdUnroll = 8;
+constexpr int kSmemBatch = 64;  // the nodes of a growing step live in shared memory up to this many
 constexpr int kChunkNodes = 64;
 constexpr int kBatchMinB = 8;    // steps of at least this many nodes select them together
 constexpr int kSortCap = 512;    // chunk maxima sorted per selection round
-constexpr int kCandCap = 256;    // candidates ranked per round; more fall back to one-by-one extraction
+constexpr int kCandCap = 256;    // candidates ranked per round, a quarter per warp; more fall back to
+                                 // one-by-one extraction
 // dynamic part (static shared variables use the rest: the sort and candidate buffers and a few words)
-constexpr int kMaxSmemBytes = 227 * 1024 - (kSortCap + 2 * kCandCap) * 8 - 1024;
+constexpr int kMaxSmemBytes = 227 * 1024 - (kSortCap + 2 * kCandCap) * 8 - kSmemBatch * 4 - 1024;
 
 struct Sub {
   int32_t start, count;  // node list range
@@ -65,6 +67,7 @@ struct IpArgs {
   uint64_t seed;
   int smem_nodes;                  // subproblems up to this size keep their state in shared memory
   int cv16;                        // node weights fit 16 bits: kept in shared memory too
+  int hv_smem;                     // the trial's fallback hashes fit in shared memory too
   int32_t *gg;                     // global fallback state per block
   uint8_t *gst;
   uint16_t *gcv;
@@ -116,19 +119,60 @@ __device__ __forceinline__ void rescan_chunk(int c, int cnt, const int32_t *g, c
 
 constexpr int kIpWarps = 4;  // warps per (subproblem, trial)
 
-// Sorts x[0, P) into descending order (P a power of two); all threads of the
-// block take part, and the block is synchronised on return.
-__device__ __forceinline__ void bitonic_desc(unsigned long long *x, int P) {
-  for (int size = 2; size <= P; size <<= 1)
+// Bitonic sort of kSortCap = 512 keys into descending order by the block's
+// 128 threads, four keys per thread in registers (thread t holds positions
+// 4t .. 4t+3): partners at distance 1 and 2 are in the same thread, at 4 .. 64
+// in the same warp (shuffles), at 128 and 256 in another warp (through x, the
+// only stages with block barriers).  On return x[0, 512) holds the sorted keys
+// and the block is synchronised.
+static_assert(kSortCap == 4 * 32 * kIpWarps, "four keys per thread");
+static_assert(kChunkNodes == 64, "two chunk nodes per lane");
+constexpr int kSegCap = kCandCap / kIpWarps;  // candidates per warp and round
+
+__device__ __forceinline__ unsigned long long keep(unsigned long long mine, unsigned long long other, bool take_max) {
+  return take_max ? (mine > other ? mine : other) : (mine < other ? mine : other);
+}
+
+__device__ __forceinline__ void sort512_desc(unsigned long long (&r)[4], unsigned long long *x) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int size = 2; size <= kSortCap; size <<= 1) {
+#pragma unroll
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
-        const int i = 2 * t - (t & (stride - 1)), j = i + stride;
-        const bool desc = (i & size) == 0;
-        const unsigned long long u = x[i], w = x[j];
-        if ((u < w) == desc) { x[i] = w; x[j] = u; }
+      if (stride >= 128) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) x[4 * t + k] = r[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int i = 4 * t + k;
+          const unsigned long long o = x[i ^ stride];
+          r[k] = keep(r[k], o, ((i & stride) == 0) == ((i & size) == 0));
+        }
+        __syncthreads();
+      } else if (stride >= 4) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int i = 4 * t + k;
+          const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, r[k], stride / 4);
+          r[k] = keep(r[k], o, ((i & stride) == 0) == ((i & size) == 0));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          if (k & stride) continue;
+          const int i = 4 * t + k;
+          const unsigned long long lo = r[k], hi = r[k | stride];
+          const bool desc = (i & size) == 0;
+          r[k] = keep(lo, hi, desc);
+          r[k | stride] = keep(lo, hi, !desc);
+        }
       }
-      __syncthreads();
     }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) x[4 * t + k] = r[k];
+  __syncthreads();
 }
 
 __device__ __forceinline__ int node_of(unsigned long long key) {
@@ -141,10 +185,11 @@ __device__ __forceinline__ int node_of(unsigned long long key) {
 // add up the trial's cut.
 __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
   extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ int s_nb, s_nz, s_nc;
+  __shared__ int s_nb, s_nz, s_wc[kIpWarps];
   __shared__ long long s_w1;
   __shared__ unsigned long long s_red[kIpWarps];
   __shared__ unsigned long long s_sort[kSortCap], s_cand[kCandCap], s_rank[kCandCap];
+  __shared__ int32_t s_batch[kSmemBatch];
   const int lane = (int)lane_id(), warp = threadIdx.x >> 5;
   const int si = blockIdx.x / a.trials, t = blockIdx.x % a.trials;
   const Sub S = a.subs[si];
@@ -155,14 +200,23 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
   int32_t *g;
   uint8_t *st;
   uint16_t *cv = nullptr;
+  uint32_t *hv = nullptr;  // fallback hashes of the trial, when shared memory has room for them
   if (cnt <= a.smem_nodes) {
     const int mch = (a.smem_nodes + kChunkNodes - 1) / kChunkNodes;
     const int msup = (mch + 31) / 32;
     best = reinterpret_cast<unsigned long long *>(dyn);
     sup = best + mch;
     g = reinterpret_cast<int32_t *>(dyn + sizeof(unsigned long long) * (mch + msup));
-    if (a.cv16) cv = reinterpret_cast<uint16_t *>(g + a.smem_nodes);
-    st = reinterpret_cast<uint8_t *>(g + a.smem_nodes) + (a.cv16 ? 2 * a.smem_nodes : 0);
+    unsigned char *tail = reinterpret_cast<unsigned char *>(g + a.smem_nodes);
+    if (a.hv_smem) {
+      hv = reinterpret_cast<uint32_t *>(tail);
+      tail += sizeof(uint32_t) * a.smem_nodes;
+    }
+    if (a.cv16) {
+      cv = reinterpret_cast<uint16_t *>(tail);
+      tail += sizeof(uint16_t) * a.smem_nodes;
+    }
+    st = tail;
   } else {
     best = a.gbest + (int64_t)blockIdx.x * a.gchunks;
     sup = a.gsup + (int64_t)blockIdx.x * ((a.gchunks + 31) / 32);
@@ -170,21 +224,20 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
     st = a.gst + (int64_t)blockIdx.x * a.gnodes;
     if (a.cv16) cv = a.gcv + (int64_t)blockIdx.x * a.gnodes;
   }
+  const uint64_t kip = stream_key(a.seed, TAG_IP, 0, (uint32_t)S.bid);
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
     g[j] = -a.dpl[start + j];
     st[j] = S_FREE;
     if (cv) cv[j] = (uint16_t)a.cvl[start + j];
+    if (hv) hv[j] = h32(kip, (uint32_t)a.vtx[start + j], (uint32_t)t);
   }
   for (int c = threadIdx.x; c < nch; c += blockDim.x) best[c] = 0;
   for (int c = threadIdx.x; c < nsup; c += blockDim.x) sup[c] = 0;
   __syncthreads();
-  const uint64_t kip = stream_key(a.seed, TAG_IP, 0, (uint32_t)S.bid);
   int64_t w1 = 0;  // warp 0's copy is the authoritative one; others read s_w1
   const int B = 1 + cnt / 1024;  // nodes per growing step
-  int32_t *batch = a.gbatch + (int64_t)blockIdx.x * a.batch_cap;
+  int32_t *batch = B <= kSmemBatch ? s_batch : a.gbatch + (int64_t)blockIdx.x * a.batch_cap;
   const bool batched = B >= kBatchMinB && cnt <= a.smem_nodes && nch <= kSortCap;
-  int P = 64;
-  while (P < nch) P <<= 1;
   for (;;) {
     if (threadIdx.x == 0) s_w1 = w1;
     __syncthreads();
@@ -202,41 +255,66 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
         const int nb0 = s_nb;
         const long long w10 = s_w1;
         if (nb0 >= B || w10 >= S.T1) break;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) s_sort[i] = i < nch ? best[i] : 0ull;
-        if (threadIdx.x == 0) { s_nz = 0; s_nc = 0; }
-        __syncthreads();
-        bitonic_desc(s_sort, P);
-        for (int i = threadIdx.x; i < P; i += blockDim.x)
-          if (s_sort[i] != 0 && (i + 1 == P || s_sort[i + 1] == 0)) s_nz = i + 1;
+        {
+          unsigned long long rk[4];
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            const int i = 4 * (int)threadIdx.x + k;
+            rk[k] = i < nch ? best[i] : 0ull;
+          }
+          if (threadIdx.x == 0) s_nz = 0;
+          sort512_desc(rk, s_sort);
+        }
+        for (int i = threadIdx.x; i < kSortCap; i += blockDim.x)
+          if (s_sort[i] != 0 && (i + 1 == kSortCap || s_sort[i + 1] == 0)) s_nz = i + 1;
         __syncthreads();
         const int nz = s_nz;
         if (nz == 0) break;  // no frontier node left
         const int q = min(B - nb0, nz);
         const unsigned long long tau = s_sort[q - 1];
-        // every frontier node with key >= tau sits in one of the q leading chunks
-        for (int r = warp; r < q; r += kIpWarps) {
-          const int c = node_of(s_sort[r]) / kChunkNodes;
-#pragma unroll
-          for (int rr = 0; rr < kChunkNodes / 32; rr++) {
-            const int j = c * kChunkNodes + rr * 32 + lane;
-            unsigned long long key = 0;
-            if (j < cnt && st[j] == S_FRONT) key = gain_key(g[j], j);
-            const bool is = key >= tau && key != 0;
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, is);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(&s_nc, __popc(m));
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            const int pos = base + __popc(m & lanemask_lt());
-            if (is && pos < kCandCap) s_cand[pos] = key;
+        // every frontier node with key >= tau sits in one of the q leading chunks; each warp
+        // gathers those of its chunks into its own segment of s_cand
+        {
+          int mine = 0;
+          unsigned long long *seg = s_cand + warp * kSegCap;
+          for (int r = warp; r < q; r += kIpWarps) {
+            const int c = node_of(s_sort[r]) / kChunkNodes;
+            const int j0 = c * kChunkNodes + lane, j1 = j0 + 32;
+            unsigned long long k0 = 0, k1 = 0;
+            if (j0 < cnt && st[j0] == S_FRONT) k0 = gain_key(g[j0], j0);
+            if (j1 < cnt && st[j1] == S_FRONT) k1 = gain_key(g[j1], j1);
+            const bool in0 = k0 != 0 && k0 >= tau, in1 = k1 != 0 && k1 >= tau;
+            const unsigned m0 = __ballot_sync(0xFFFFFFFFu, in0), m1 = __ballot_sync(0xFFFFFFFFu, in1);
+            const int p0 = mine + __popc(m0 & lanemask_lt());
+            const int p1 = mine + __popc(m0) + __popc(m1 & lanemask_lt());
+            if (in0 && p0 < kSegCap) seg[p0] = k0;
+            if (in1 && p1 < kSegCap) seg[p1] = k1;
+            mine += __popc(m0) + __popc(m1);
           }
+          if (lane == 0) s_wc[warp] = mine;
         }
         __syncthreads();
-        const int C = s_nc;
-        if (C > kCandCap) { seq = true; break; }
-        for (int i = threadIdx.x; i < C; i += blockDim.x) {  // keys are distinct: rank = place
-          const unsigned long long x = s_cand[i];
+        int wc[kIpWarps], C = 0;
+        bool over = false;
+#pragma unroll
+        for (int w2 = 0; w2 < kIpWarps; w2++) {
+          wc[w2] = s_wc[w2];
+          C += wc[w2];
+          over = over || wc[w2] > kSegCap;
+        }
+        if (over) { seq = true; break; }
+        for (int t = threadIdx.x; t < C; t += blockDim.x) {  // keys are distinct: rank = place
+          int at = -1, acc = 0;
+#pragma unroll
+          for (int w3 = 0; w3 < kIpWarps; w3++) {
+            if (at < 0 && t < acc + wc[w3]) at = w3 * kSegCap + (t - acc);
+            acc += wc[w3];
+          }
+          const unsigned long long x = s_cand[at];
           int r = 0;
-          for (int i2 = 0; i2 < C; i2++) r += s_cand[i2] > x ? 1 : 0;
+#pragma unroll
+          for (int w3 = 0; w3 < kIpWarps; w3++)
+            for (int i2 = 0; i2 < wc[w3]; i2++) r += s_cand[w3 * kSegCap + i2] > x ? 1 : 0;
           s_rank[r] = x;
         }
         __syncthreads();
@@ -282,7 +360,26 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
           if (lane == 0) { s_nb = nb; s_w1 = w; }
         }
         __syncthreads();
-        for (int r = warp; r < q; r += kIpWarps) rescan_chunk(node_of(s_sort[r]) / kChunkNodes, cnt, g, st, best);
+        // the q leading chunks' maxima again, two chunks per warp at a time
+        for (int r = warp; r < q; r += 2 * kIpWarps) {
+          const bool two = r + kIpWarps < q;
+          const int ca = node_of(s_sort[r]) / kChunkNodes;
+          const int cb = two ? node_of(s_sort[r + kIpWarps]) / kChunkNodes : ca;
+          unsigned long long ba = 0, bb = 0;
+#pragma unroll
+          for (int rr = 0; rr < kChunkNodes / 32; rr++) {
+            const int ja = ca * kChunkNodes + rr * 32 + lane, jb = cb * kChunkNodes + rr * 32 + lane;
+            const bool fa = ja < cnt && st[ja] == S_FRONT, fb = jb < cnt && st[jb] == S_FRONT;
+            if (fa) { const unsigned long long k = gain_key(g[ja], ja); ba = k > ba ? k : ba; }
+            if (fb) { const unsigned long long k = gain_key(g[jb], jb); bb = k > bb ? k : bb; }
+          }
+          ba = wmax_u64(ba);
+          bb = wmax_u64(bb);
+          if (lane == 0) {
+            best[ca] = ba;
+            if (two) best[cb] = bb;
+          }
+        }
       }
       __syncthreads();
       if (seq) {  // the chunk groups' maxima again for the one-by-one walk
@@ -336,8 +433,8 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
         if (st[jj] != S_FREE) continue;
         const int cjj = cv ? (int)cv[jj] : a.cvl[start + jj];
         if (w1 + cjj > S.L1) continue;
-        const unsigned long long key =
-            ((unsigned long long)h32(kip, (uint32_t)a.vtx[start + jj], (uint32_t)t) << 32) | (unsigned)jj;
+        const uint32_t h = hv ? hv[jj] : h32(kip, (uint32_t)a.vtx[start + jj], (uint32_t)t);
+        const unsigned long long key = ((unsigned long long)h << 32) | (unsigned)jj;
         m = key < m ? key : m;
       }
       m = wmin_u64(m);
@@ -408,8 +505,9 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_ip_grow(IpArgs a) {
       }
     }
     __syncthreads();
-    // the maxima over 32 chunks again, from the raised chunk maxima (one warp per group)
-    for (int sc = warp; sc < nsup; sc += kIpWarps) {
+    // the maxima over 32 chunks again, from the raised chunk maxima (one warp per group); the
+    // batched selection reads the chunk maxima alone
+    for (int sc = warp; sc < (batched ? 0 : nsup); sc += kIpWarps) {
       const int c = sc * 32 + lane;
       const unsigned long long x = wmax_u64(c < nch ? best[c] : 0ull);
       if (lane == 0) sup[sc] = x;
@@ -635,9 +733,13 @@ void initial_partition(gp_ctx *ctx, const DevGraph &g, int32_t k, int64_t eps_pp
     a.subs = dsub.get(); a.trials = trials; a.n = n; a.seed = seed;
     a.cv16 = cvmax <= 65535 ? 1 : 0;
     // shared-memory state: chunk maxima (8 B per 64 nodes) + gain (4 B) + weight (2 B, when it fits) +
-    // state (1 B) per node
-    const int per_node = a.cv16 ? 7 : 5;
-    const int smem_cap = (kMaxSmemBytes - 128) * kChunkNodes / (9 + per_node * kChunkNodes);
+    // state (1 B) per node, and the fallback hash (4 B) when that still holds every subproblem of
+    // this depth
+    int per_node = a.cv16 ? 7 : 5;
+    auto cap_for = [&](int pn) { return (kMaxSmemBytes - 128) * kChunkNodes / (9 + pn * kChunkNodes); };
+    a.hv_smem = maxcnt <= cap_for(per_node + 4) ? 1 : 0;
+    if (a.hv_smem) per_node += 4;
+    const int smem_cap = cap_for(per_node);
     a.smem_nodes = std::max(1, std::min(maxcnt, smem_cap));
     const int mch = (a.smem_nodes + kChunkNodes - 1) / kChunkNodes;
     const size_t smem_bytes = (size_t)(mch + (mch + 31) / 32) * 8 + (size_t)a.smem_nodes * per_node;

@@ -577,15 +577,26 @@ __global__ void __launch_bounds__(kThreads) k_compact_dirty(const int4 *list, co
   const int lane = (int)lane_id();
   for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += gridDim.x * blockDim.x) {
     const int i = base + (int)threadIdx.x;
-    int b = -1;
+    int bk = k1;  // bucket of the position (k1 past the end)
+    int b = -1;   // bucket if the record is kept
     int4 rec = make_int4(0, 0, 0, 0);
     if (i < end) {
-      b = k0;
-      while (b + 1 < k1 && offs[b + 1] <= i) b++;
+      bk = k0;
+      while (bk + 1 < k1 && offs[bk + 1] <= i) bk++;
       rec = list[i];
-      if (!dirty[rec.x]) b = -1;
+      if (dirty[rec.x]) b = bk;
     }
-    const unsigned peers = __match_any_sync(FULL, b >= 0 ? b : -1 - lane);
+    // consecutive lanes hold consecutive list positions, so a bucket's lanes form one run:
+    // its kept lanes are the peers (no match over arbitrary keys needed)
+    const int prev = __shfl_up_sync(FULL, bk, 1);
+    const unsigned starts = __ballot_sync(FULL, lane == 0 || prev != bk);
+    const unsigned kept = __ballot_sync(FULL, b >= 0);
+    const unsigned le = lanemask_lt() | (1u << lane);
+    const unsigned after = starts & ~le;  // run starts after this lane
+    const unsigned run_lo = 31 - __clz(starts & le);
+    const unsigned run_hi = after ? (unsigned)__ffs(after) - 1 : 32u;  // one past the run
+    const unsigned run = (run_hi == 32 ? FULL : ((1u << run_hi) - 1u)) & ~((1u << run_lo) - 1u);
+    const unsigned peers = kept & run;
     if (b >= 0) {
       const int leader = __ffs(peers) - 1;
       int pos = 0;
@@ -597,7 +608,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_dirty(const int4 *list, co
 }
 
 // Every applied move makes its node and the node's neighbours dirty (a warp
-// per move reads the row).
+// takes two moves at a time and reads both rows side by side).
 __global__ void __launch_bounds__(kThreads) k_mark_dirty(const int4 *mov, int nmov, const uint64_t *ov_key,
                                                          const uint32_t *ov_val, const uint8_t *ov_acc, int nov,
                                                          const uint64_t *cutoff, uint64_t kprio,
@@ -607,18 +618,30 @@ __global__ void __launch_bounds__(kThreads) k_mark_dirty(const int4 *mov, int nm
   const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const int total = nmov + nov;
-  for (int t = wid; t < total; t += nw) {
-    int v;
-    if (t < nmov) {
-      v = mov[t].x;
-    } else {
-      if (!ov_acc[t - nmov]) continue;
-      v = (int)ov_val[t - nmov];
+  for (int t0 = 2 * wid; t0 < total; t0 += 2 * nw) {
+    int v[2], e0[2], e1[2];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const int t = t0 + q;
+      v[q] = -1;
+      if (t < nmov) v[q] = mov[t].x;
+      else if (t < total && ov_acc[t - nmov]) v[q] = (int)ov_val[t - nmov];
+      if (v[q] >= 0 && cutoff &&
+          ((((uint64_t)h32(kprio, (uint32_t)v[q], 0)) << 32) | (uint32_t)v[q]) >= *cutoff)
+        v[q] = -1;
+      e0[q] = v[q] >= 0 ? xadj[v[q]] : 0;
+      e1[q] = v[q] >= 0 ? xadj[v[q] + 1] : 0;
     }
-    if (cutoff && ((((uint64_t)h32(kprio, (uint32_t)v, 0)) << 32) | (uint32_t)v) >= *cutoff) continue;
-    const int e0 = xadj[v], e1 = xadj[v + 1];
-    if (lane == 0) dirty[v] = 1;
-    for (int e = e0 + lane; e < e1; e += 32) dirty[adjncy[e]] = 1;
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+      if (lane == 0 && v[q] >= 0) dirty[v[q]] = 1;
+    const int len = max(e1[0] - e0[0], e1[1] - e0[1]);
+    for (int o = lane; o < len; o += 32) {
+      const int a0 = e0[0] + o, a1 = e0[1] + o;
+      const int u0 = a0 < e1[0] ? adjncy[a0] : -1, u1 = a1 < e1[1] ? adjncy[a1] : -1;
+      if (u0 >= 0) dirty[u0] = 1;
+      if (u1 >= 0) dirty[u1] = 1;
+    }
   }
 }
 
@@ -1465,7 +1488,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
           k_apply<<<ga, kThreads, sizeof(int) * aa.nshared, ctx->stream>>>(aa);
           GP_LAUNCH_CHECK();
           if (use_dirty) {
-            k_mark_dirty<<<grid_for((int64_t)(nmov + nov) * 32, kThreads, grid), kThreads, 0, ctx->stream>>>(
+            k_mark_dirty<<<grid_for((int64_t)(nmov + nov) * 16, kThreads, grid), kThreads, 0, ctx->stream>>>(
                 mov.get(), nmov, ov_key.get(), ov_val.get(), ov_acc.get(), nov, aa.cutoff, kprio, g.xadj, g.adjncy,
                 dirty.get());
             GP_LAUNCH_CHECK();

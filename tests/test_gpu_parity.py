@@ -214,10 +214,10 @@ def test_initial_partition_large_subproblem_uses_global_state(gp, ctx):
 @pytest.mark.parametrize("name", ["er", "er_heavy", "grid", "star", "rmat"])
 def test_initial_partition_steps_of_many_nodes_match_oracle(gp, ctx, name):
     """Subproblems of 8k-30k nodes (growing steps of B = 8..30 nodes, selected together): plain
-    ER; ER with node weights up to 5000 (nodes that no longer fit are retired mid-step); a grid
+    ER (24k nodes: state in shared memory, fallback hashes not); ER with node weights up to 5000 (nodes that no longer fit are retired mid-step); a grid
     (many equal gains); a star (after the centre every leaf has the same gain, so the candidates
     overflow the ranked set and the step falls back to one-by-one extraction); R-MAT."""
-    g = {"er": lambda: gg.er(20000, 90000, 21),
+    g = {"er": lambda: gg.er(24000, 100000, 21),
          "er_heavy": lambda: gg.with_node_weights(gg.er(16000, 70000, 22), 5000),
          "grid": lambda: gg.grid2d(110, 100),
          "star": lambda: star(10000),
