@@ -288,10 +288,11 @@ gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, dou
  * Many independent graphs partitioned at once (no counterpart in the paper:
  * a throughput form of gp_partition for batches of small or mid-sized
  * graphs, whose levels are too small to fill the GPU one graph at a time).
- * `workers` host threads (1..64), each with its own stream and memory pool
- * kept in the context, take the items largest first and run the same
- * partition as gp_partition on each, so every item's blocks and cut equal
- * those of a gp_partition call with the same arguments.  Work already queued
+ * Items the batched engine takes (gp_batch_tuning below) are partitioned by
+ * its persistent kernel; for the others `workers` host threads (1..64), each
+ * with its own stream and memory pool kept in the context, take the items
+ * largest first and run gp_partition on each.  Every item's blocks and cut
+ * equal those of a gp_partition call with the same arguments.  Work already queued
  * on the context stream is waited for first.  Per item: `blocks` (device,
  * g.n entries, caller-owned) and, on return, `cut` and `status` (the item's
  * own result; its message is lost).  Returns GP_OK when every item succeeded,
@@ -306,9 +307,55 @@ typedef struct gp_batch_item {
   int32_t *blocks;
   int64_t cut;
   gp_status status;
+  int32_t engine;              /* out: 1 if the item ran on the batched engine, 0 on the per-graph path */
+  gp_partition_stats *stats;   /* host, may be NULL: the item's per-level records (device times 0 on
+                                  the engine) */
 } gp_batch_item;
 gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32_t count, int32_t workers,
                              const gp_config *cfg);
+
+/*
+ * The batched engine of gp_partition_batch (no counterpart in the paper).
+ * Items of at most max_entries CSR entries and max_nodes nodes run on one
+ * persistent kernel: each CTA takes whole graphs from a device-side queue
+ * (largest first) and partitions each inside the CTA -- the same method and
+ * readings as gp_partition, so the results are identical -- with its hierarchy
+ * and scratch in a per-CTA arena.  The other items, and engine items whose
+ * hierarchy outgrows the arena, run on the per-graph path (the worker
+ * contexts above), after the engine.  The configuration must use a sparsifier
+ * other than GP_SPARSIFY_TWEIGHT_EXACT, at most 254 sub-rounds and at least one
+ * bisection trial; otherwise every item takes the per-graph path.
+ *
+ * gp_batch_autotune measures, on the items given (grouped into size classes
+ * by their CSR entries, class c holding (class_entries[c-1],
+ * class_entries[c]]), the engine's graphs/s with each CTA size and the
+ * per-graph path's graphs/s with `workers` workers, and picks the CTA size
+ * and the largest class up to which the engine wins; the items' outputs are
+ * not written.  The result is installed in the context (gp_batch_set_tuning)
+ * and returned in *out (may be NULL).  Synchronises.
+ */
+#define GP_TUNE_CLASSES 12
+typedef struct gp_batch_tuning {
+  int32_t engine;             /* 1: use the engine; 0: per-graph path only */
+  int32_t threads;            /* engine CTA size: 256, 512 or 1024 */
+  int64_t max_entries;        /* engine items have at most this many CSR entries ... */
+  int64_t max_nodes;          /* ... and at most this many nodes */
+  int64_t arena_cap_bytes;    /* device memory all arenas may take (0: a third of the free memory) */
+  int64_t arena_bytes;        /* arena per CTA (0: estimated from the largest engine item) */
+  int32_t classes;            /* autotuner: size classes it measured */
+  int32_t pad;
+  int64_t class_entries[GP_TUNE_CLASSES];    /* upper end of each class (CSR entries) */
+  int32_t class_items[GP_TUNE_CLASSES];      /* items of the class in the tuning set */
+  int32_t class_threads[GP_TUNE_CLASSES];    /* fastest engine CTA size on the class */
+  double class_engine_gps[GP_TUNE_CLASSES];  /* engine graphs/s on the class with that CTA size */
+  double class_path_gps[GP_TUNE_CLASSES];    /* per-graph path graphs/s on the class (0: not measured) */
+  double tune_ms;                            /* wall time of the tuning */
+} gp_batch_tuning;
+void gp_batch_tuning_default(gp_batch_tuning *t);
+gp_status gp_batch_set_tuning(gp_ctx *ctx, const gp_batch_tuning *t);
+gp_status gp_batch_get_tuning(gp_ctx *ctx, gp_batch_tuning *t);
+gp_status gp_batch_autotune(gp_ctx *ctx, const gp_batch_item *items, int32_t count, int32_t workers,
+                            const gp_config *cfg, gp_batch_tuning *out);
 
 /*
  * Serving (no counterpart in the paper): a request loop for partition

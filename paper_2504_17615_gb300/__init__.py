@@ -41,7 +41,32 @@ class gp_graph(ctypes.Structure):
 
 class gp_batch_item(ctypes.Structure):
     _fields_ = [("g", gp_graph), ("k", ctypes.c_int32), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("blocks", ctypes.c_void_p), ("cut", ctypes.c_int64), ("status", ctypes.c_int)]
+                ("blocks", ctypes.c_void_p), ("cut", ctypes.c_int64), ("status", ctypes.c_int),
+                ("engine", ctypes.c_int32), ("stats", ctypes.c_void_p)]
+
+
+GP_TUNE_CLASSES = 12
+
+
+class gp_batch_tuning(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_int32), ("threads", ctypes.c_int32), ("max_entries", ctypes.c_int64),
+                ("max_nodes", ctypes.c_int64), ("arena_cap_bytes", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_int64), ("classes", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("class_entries", ctypes.c_int64 * GP_TUNE_CLASSES),
+                ("class_items", ctypes.c_int32 * GP_TUNE_CLASSES),
+                ("class_threads", ctypes.c_int32 * GP_TUNE_CLASSES),
+                ("class_engine_gps", ctypes.c_double * GP_TUNE_CLASSES),
+                ("class_path_gps", ctypes.c_double * GP_TUNE_CLASSES), ("tune_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f in ("engine", "threads", "max_entries", "max_nodes", "arena_cap_bytes",
+                                           "arena_bytes", "classes", "tune_ms")}
+        d["class_table"] = [{"max_entries": self.class_entries[i], "items": self.class_items[i],
+                             "engine_threads": self.class_threads[i],
+                             "engine_graphs_per_s": self.class_engine_gps[i],
+                             "path_graphs_per_s": self.class_path_gps[i]}
+                            for i in range(self.classes) if self.class_items[i] > 0]
+        return d
 
 
 class gp_request(ctypes.Structure):
@@ -159,6 +184,11 @@ def _load():
                                                ctypes.POINTER(d)]),
             "gp_measure_random_reads": (ctypes.c_int, [P, i64, i64, ctypes.POINTER(d)]),
             "gp_partition_batch": (ctypes.c_int, [P, ctypes.POINTER(gp_batch_item), i32, i32, C]),
+            "gp_batch_tuning_default": (None, [ctypes.POINTER(gp_batch_tuning)]),
+            "gp_batch_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(gp_batch_tuning)]),
+            "gp_batch_get_tuning": (ctypes.c_int, [P, ctypes.POINTER(gp_batch_tuning)]),
+            "gp_batch_autotune": (ctypes.c_int, [P, ctypes.POINTER(gp_batch_item), i32, i32, C,
+                                                 ctypes.POINTER(gp_batch_tuning)]),
             "gp_server_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, i32, i64, C]),
             "gp_server_submit": (ctypes.c_int, [P, ctypes.POINTER(gp_request), ctypes.POINTER(i64)]),
             "gp_server_wait": (ctypes.c_int, [P, i64, ctypes.POINTER(gp_response)]),
@@ -398,24 +428,61 @@ class Context:
                                           blocks.data_ptr(), ctypes.byref(cut), ctypes.byref(st)))
         return blocks[:g.n], cut.value, st
 
-    def gp_partition_batch(self, jobs, workers: int = 8, cfg: gp_config | None = None, check: bool = True):
-        """jobs: list of (graph, k, eps, seed).  Returns [(blocks tensor, cut)] in job order
-        ([(blocks, cut, status)] without raising when check is False)."""
+    def _batch_items(self, jobs, with_stats=False):
         torch = self.torch
         arr = (gp_batch_item * max(len(jobs), 1))()
-        outs = []
+        outs, stats = [], []
         for i, (g, k, eps, seed) in enumerate(jobs):
             b = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
             outs.append(b)
             arr[i].g = g.struct()
             arr[i].k, arr[i].eps, arr[i].seed = k, eps, seed
             arr[i].blocks = b.data_ptr()
+            if with_stats:
+                st = gp_partition_stats()
+                stats.append(st)
+                arr[i].stats = ctypes.addressof(st)
+        return arr, outs, stats
+
+    def gp_partition_batch(self, jobs, workers: int = 8, cfg: gp_config | None = None, check: bool = True,
+                           details: bool = False):
+        """jobs: list of (graph, k, eps, seed).  Returns [(blocks tensor, cut)] in job order
+        ([(blocks, cut, status)] without raising when check is False; with details, every tuple
+        also carries the item's engine flag and its gp_partition_stats)."""
+        arr, outs, stats = self._batch_items(jobs, with_stats=details)
         st = self.lib.gp_partition_batch(self.ptr, arr, len(jobs), workers,
                                          ctypes.byref(cfg) if cfg is not None else None)
-        if not check:
-            return [(outs[i][:jobs[i][0].n], arr[i].cut, arr[i].status) for i in range(len(jobs))]
-        self._check(st)
-        return [(outs[i][:jobs[i][0].n], arr[i].cut) for i in range(len(jobs))]
+        if check:
+            self._check(st)
+        res = []
+        for i in range(len(jobs)):
+            r = (outs[i][:jobs[i][0].n], arr[i].cut) + (() if check else (arr[i].status,))
+            if details:
+                r = r + (arr[i].engine, stats[i])
+            res.append(r)
+        return res
+
+    def batch_tuning(self) -> gp_batch_tuning:
+        t = gp_batch_tuning()
+        self._check(self.lib.gp_batch_get_tuning(self.ptr, ctypes.byref(t)))
+        return t
+
+    def batch_set_tuning(self, **kw) -> gp_batch_tuning:
+        """Engine settings; fields not given keep their defaults (gp_batch_tuning_default)."""
+        t = gp_batch_tuning()
+        self.lib.gp_batch_tuning_default(ctypes.byref(t))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        self._check(self.lib.gp_batch_set_tuning(self.ptr, ctypes.byref(t)))
+        return t
+
+    def batch_autotune(self, jobs, workers: int = 8, cfg: gp_config | None = None) -> gp_batch_tuning:
+        arr, outs, _ = self._batch_items(jobs)
+        t = gp_batch_tuning()
+        self._check(self.lib.gp_batch_autotune(self.ptr, arr, len(jobs), workers,
+                                               ctypes.byref(cfg) if cfg is not None else None,
+                                               ctypes.byref(t)))
+        return t
 
     def gp_partition_host(self, n: int, m2: int, xadj, adjncy, vwgt, adjwgt, k: int, eps: float,
                           seed: int, cfg: gp_config | None = None, blocks=None):

@@ -1,13 +1,83 @@
-// batch.cu -- many independent graphs partitioned at once.  Each worker is
-// a context of its own (stream, memory pool) driven by its own host thread;
-// the level loops of different graphs then overlap on the GPU, which a
-// single small graph cannot fill.  Every item runs the same partition_impl
-// as gp_partition, so the results do not depend on the batching.
+// batch.cu -- many independent graphs partitioned at once.
+//
+// Items the batched engine takes (engine.cu) run there first: one persistent
+// launch whose CTAs partition whole graphs.  The rest run on the per-graph
+// path: each worker is a context of its own (stream, memory pool) driven by
+// its own host thread, so the level loops of different graphs overlap on the
+// GPU, which a single small graph cannot fill.  Every item, on either path,
+// follows the same method and readings as gp_partition, so the results do not
+// depend on the batching.
 #include "gp_internal.cuh"
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <thread>
+
+namespace gp {
+
+void ensure_batch_workers(gp_ctx *ctx, int workers) {
+  GP_CUDA(cudaSetDevice(ctx->device));
+  while ((int)ctx->workers.size() < workers) {
+    cudaStream_t s = nullptr;
+    GP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    gp_ctx *w = nullptr;
+    const gp_status st = gp_create(&w, ctx->device, (void *)s, nullptr);
+    if (st != GP_OK) {
+      cudaStreamDestroy(s);
+      fail(st, "gp_partition_batch: creating a worker failed");
+    }
+    ctx->workers.push_back(w);
+  }
+  for (int i = 0; i < workers; i++) ctx->workers[(size_t)i]->device_share = workers;
+  // inputs may still be in flight on the caller's stream
+  cudaEvent_t ready;
+  GP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  GP_CUDA(cudaEventRecord(ready, ctx->stream));
+  for (int i = 0; i < workers; i++) GP_CUDA(cudaStreamWaitEvent(ctx->workers[(size_t)i]->stream, ready, 0));
+  GP_CUDA(cudaEventDestroy(ready));
+}
+
+void batch_per_graph(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx, int workers,
+                     const gp_config &cfg) {
+  if (idx.empty()) return;
+  ensure_batch_workers(ctx, workers);
+  std::vector<int32_t> order(idx);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return items[a].g.m2 > items[b].g.m2; });
+  std::atomic<size_t> next{0};
+  auto run = [&](gp_ctx *w) {
+    cudaSetDevice(w->device);
+    for (;;) {
+      const size_t j = next.fetch_add(1);
+      if (j >= order.size()) break;
+      gp_batch_item &it = items[order[j]];
+      it.cut = 0;
+      it.engine = 0;
+      it.status = gp_partition(w, &it.g, it.k, it.eps, it.seed, &cfg, it.blocks, &it.cut, it.stats);
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int i = 1; i < workers; i++) threads.emplace_back(run, ctx->workers[(size_t)i]);
+  run(ctx->workers[0]);
+  for (auto &t : threads) t.join();
+}
+
+}  // namespace gp
+
+namespace {
+
+// The argument checks gp_partition makes before any launch.
+gp_status item_check(const gp_batch_item &it) {
+  const gp_graph &g = it.g;
+  if (g.n < 0 || g.m2 < 0 || g.m2 >= ((int64_t)1 << 31)) return GP_ERR_INVALID;
+  if (g.n > 0 && (!g.xadj || !g.vwgt)) return GP_ERR_INVALID;
+  if (g.m2 > 0 && (!g.adjncy || !g.adjwgt)) return GP_ERR_INVALID;
+  if (g.n > 0 && !it.blocks) return GP_ERR_INVALID;
+  if (it.k < 1 || !(it.eps > 0 && it.eps < 1000) || llround(it.eps * 1e6) < 1) return GP_ERR_INVALID;
+  return GP_OK;
+}
+
+}  // namespace
 
 extern "C" gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32_t count, int32_t workers,
                                         const gp_config *cfg) {
@@ -19,48 +89,23 @@ extern "C" gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32
   gp_config c;
   if (cfg) c = *cfg;
   else gp_config_default(&c);
+  std::vector<int32_t> valid;
+  for (int32_t i = 0; i < count; i++) {
+    items[i].cut = 0;
+    items[i].engine = 0;
+    items[i].status = item_check(items[i]);
+    if (items[i].status == GP_OK) valid.push_back(i);
+  }
   try {
     GP_CUDA(cudaSetDevice(ctx->device));
-    while ((int)ctx->workers.size() < workers) {
-      cudaStream_t s = nullptr;
-      GP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-      gp_ctx *w = nullptr;
-      const gp_status st = gp_create(&w, ctx->device, (void *)s, nullptr);
-      if (st != GP_OK) {
-        cudaStreamDestroy(s);
-        gp::fail(st, "gp_partition_batch: creating a worker failed");
-      }
-      ctx->workers.push_back(w);
-    }
-    for (int i = 0; i < workers; i++) ctx->workers[i]->device_share = workers;
-    // inputs may still be in flight on the caller's stream
-    cudaEvent_t ready;
-    GP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    GP_CUDA(cudaEventRecord(ready, ctx->stream));
-    for (int i = 0; i < workers; i++) GP_CUDA(cudaStreamWaitEvent(ctx->workers[i]->stream, ready, 0));
-    GP_CUDA(cudaEventDestroy(ready));
+    const gp_batch_tuning &t = gp::batch_tuning(ctx);
+    std::vector<int32_t> rest = valid;
+    if (t.engine && gp::engine_config_ok(c)) rest = gp::engine_run(ctx, items, valid, c, t, nullptr);
+    gp::batch_per_graph(ctx, items, rest, workers, c);
   } catch (const gp::Error &e) {
     ctx->last_error = e.msg;
     return e.status;
   }
-  std::vector<int32_t> order((size_t)count);
-  for (int32_t i = 0; i < count; i++) order[(size_t)i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return items[a].g.m2 > items[b].g.m2; });
-  std::atomic<int32_t> next{0};
-  auto run = [&](gp_ctx *w) {
-    cudaSetDevice(w->device);
-    for (;;) {
-      const int32_t j = next.fetch_add(1);
-      if (j >= count) break;
-      gp_batch_item &it = items[order[(size_t)j]];
-      it.cut = 0;
-      it.status = gp_partition(w, &it.g, it.k, it.eps, it.seed, &c, it.blocks, &it.cut, nullptr);
-    }
-  };
-  std::vector<std::thread> threads;
-  for (int i = 1; i < workers; i++) threads.emplace_back(run, ctx->workers[(size_t)i]);
-  run(ctx->workers[0]);
-  for (auto &t : threads) t.join();
   for (int32_t i = 0; i < count; i++) {
     if (items[i].status != GP_OK) {
       ctx->last_error = "gp_partition_batch: item " + std::to_string(i) + " failed";

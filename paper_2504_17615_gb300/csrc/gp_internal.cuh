@@ -115,6 +115,8 @@ struct gp_ctx {
   std::vector<gp_ctx *> workers;                 // batch workers (own streams and pools)
   int64_t wait_spins = 0;                        // limit of device-side waits (0: default)
   int device_share = 1;  // contexts sharing the device (batch / server workers): persistent grids shrink
+  gp_batch_tuning tuning{};        // batched engine settings (gp_batch_set_tuning / gp_batch_autotune)
+  bool tuning_set = false;
   cudaStream_t copy_streams[4] = {};  // host-to-device copies of large inputs
   cudaEvent_t copy_events[5] = {};
 };
@@ -445,5 +447,16 @@ void modularity(gp_ctx *ctx, const DevGraph &g, const int32_t *labels, int32_t n
 void check_blocks(gp_ctx *ctx, const int32_t *blocks, int n, int k);
 void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, uint64_t seed,
                     const gp_config &cfg, int32_t *blocks, int64_t *cut_out, gp_partition_stats *st);
+
+// Batched form (batch.cu, engine.cu): the worker contexts, the per-graph path
+// over a list of items, the engine over a list of items (returns the items it
+// left to the per-graph path: not taken, or hierarchy too large for its arena).
+void ensure_batch_workers(gp_ctx *ctx, int workers);
+void batch_per_graph(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx, int workers,
+                     const gp_config &cfg);
+bool engine_config_ok(const gp_config &cfg);
+std::vector<int32_t> engine_run(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx,
+                                const gp_config &cfg, const gp_batch_tuning &t, double *engine_ms);
+const gp_batch_tuning &batch_tuning(gp_ctx *ctx);
 
 }  // namespace gp
