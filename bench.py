@@ -505,10 +505,12 @@ def batch_mix(count, nmax, seed, place=None):
     return jobs
 
 
-def batch_summary(gp, count, nmax, workers, warmup, steps):
-    """Batched form: the same graphs one gp_partition call after another, then all at once through
-    gp_partition_batch; graphs/s of both (best of `steps` passes after `warmup`), and whether the
-    results agree item by item."""
+def batch_summary(gp, count, nmax, workers, warmup, steps, serial=True):
+    """Batched form on the same graphs: one gp_partition call after another (serial), the per-graph
+    path of gp_partition_batch alone (host worker threads, engine off), and gp_partition_batch with
+    the batched engine after gp_batch_autotune has picked its CTA size and the engine/per-graph split
+    on this batch.  graphs/s of each (best of `steps` passes after `warmup`), and whether the results
+    agree item by item."""
     import torch
     t = time.time()
     ctx = gp.Context(0)
@@ -516,34 +518,54 @@ def batch_summary(gp, count, nmax, workers, warmup, steps):
     dev = [(dg, k, e, sd) for (dg, _), k, e, sd in jobs]
     torch.cuda.synchronize()
     log(f"[bench] generated and uploaded {len(jobs)} graphs in {time.time() - t:.1f}s")
-    serial = batched = None
-    for rep in range(warmup + steps):
-        t = time.perf_counter()
-        ser = [ctx.gp_partition(dg, k, e, sd)[:2] for dg, k, e, sd in dev]
-        torch.cuda.synchronize()
-        ts = time.perf_counter() - t
-        t = time.perf_counter()
-        bat = ctx.gp_partition_batch(dev, workers=workers)
-        torch.cuda.synchronize()
-        tb = time.perf_counter() - t
-        if rep >= warmup:
-            serial = ts if serial is None else min(serial, ts)
-            batched = tb if batched is None else min(batched, tb)
-    same = all(c1 == c2 and torch.equal(b1, b2) for (b1, c1), (b2, c2) in zip(ser, bat))
+
+    def timed(fn):
+        best, out = None, None
+        for rep in range(warmup + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if rep >= warmup:
+                best = dt if best is None else min(best, dt)
+        return best, out
+
+    res = {}
+    if serial:
+        ts, ser = timed(lambda: [ctx.gp_partition(dg, k, e, sd)[:2] for dg, k, e, sd in dev])
+        res["serial"] = ser
+    ctx.batch_set_tuning(engine=0)
+    tw, wrk = timed(lambda: ctx.gp_partition_batch(dev, workers=workers))
+    t0 = time.perf_counter()
+    tun = ctx.batch_autotune(dev, workers=workers)
+    tune_s = time.perf_counter() - t0
+    te, eng = timed(lambda: ctx.gp_partition_batch(dev, workers=workers, details=True))
+    n_engine = sum(1 for r in eng if r[2])
+    ref = res.get("serial", wrk)
+    same = all(c1 == c2 == c3 and torch.equal(b1, b2) and torch.equal(b1, b3)
+               for (b1, c1), (b2, c2), (b3, c3, _, _) in zip(ref, wrk, eng))
+    ctx.batch_set_tuning()
     ctx.close()
-    return {"graphs_per_s": len(jobs) / batched, "serial_graphs_per_s": len(jobs) / serial,
-            "speedup": serial / batched, "identical_results": same, "graphs": len(jobs),
-            "edges": sum(m for (_, m), _, _, _ in jobs), "workers": workers,
-            "timing": f"best of {steps} pass(es) after {warmup}, host wall clock around each pass",
-            "workload": f"{len(jobs)} graphs, n log-uniform in [1e3, {nmax:g}], ER deg 8-32 / 2D grid / 3D grid / "
-                        "R-MAT ef 8, k in {2..64}, eps 0.03 (C4 mix)"}
+    out = {"graphs_per_s": len(jobs) / te, "worker_path_graphs_per_s": len(jobs) / tw,
+           "speedup_vs_worker_path": tw / te, "identical_results": same, "graphs": len(jobs),
+           "engine_items": n_engine, "edges": sum(m for (_, m), _, _, _ in jobs), "workers": workers,
+           "tuning": tun.as_dict(), "tune_s": tune_s,
+           "timing": f"best of {steps} pass(es) after {warmup}, host wall clock around each pass "
+                     "(tuning outside the timed passes)",
+           "workload": f"{len(jobs)} graphs, n log-uniform in [1e3, {nmax:g}], ER deg 8-32 / 2D grid / 3D grid / "
+                       "R-MAT ef 8, k in {2..64}, eps 0.03 (C4 mix)"}
+    if serial:
+        out.update({"serial_graphs_per_s": len(jobs) / ts, "speedup": ts / te})
+    return out
 
 
 def run_batch(args):
     import paper_2504_17615_gb300 as gp
     from paper_2504_17615_gb300 import build as gpbuild
     gpbuild.build()
-    out = batch_summary(gp, args.batch_count, args.batch_nmax, args.batch_workers, args.warmup, args.steps)
+    out = batch_summary(gp, args.batch_count, args.batch_nmax, args.batch_workers, args.warmup, args.steps,
+                        serial=not args.batch_no_serial)
     out.update({"metric": "batched graphs/s", "value": out["graphs_per_s"], "unit": "graphs/s",
                 "steps": args.steps, "warmup": args.warmup, "config": {"workload": out["workload"]}})
     print(json.dumps(out), flush=True)
@@ -701,6 +723,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-nmax", type=float, default=1e5)
     ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--batch-no-serial", action="store_true",
+                    help="batched form: leave out the one-call-after-another pass (large batches)")
     ap.add_argument("--serve", action="store_true",
                     help="served form: Poisson request stream through the request loop, p50/p99 latency")
     ap.add_argument("--serve-count", type=int, default=128)
