@@ -308,8 +308,8 @@ typedef struct gp_batch_item {
   int64_t cut;
   gp_status status;
   int32_t engine;              /* out: 1 if the item ran on the batched engine, 0 on the per-graph path */
-  gp_partition_stats *stats;   /* host, may be NULL: the item's per-level records (device times 0 on
-                                  the engine) */
+  gp_partition_stats *stats;   /* host, may be NULL: the item's per-level records; on the engine the
+                                  phase times are the item's CTA time (SM cycles at the peak clock) */
 } gp_batch_item;
 gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32_t count, int32_t workers,
                              const gp_config *cfg);

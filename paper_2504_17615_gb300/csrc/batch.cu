@@ -16,7 +16,9 @@
 
 namespace gp {
 
-void ensure_batch_workers(gp_ctx *ctx, int workers) {
+void batch_per_graph(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx, int workers,
+                     const gp_config &cfg, int share, cudaEvent_t ready) {
+  if (idx.empty()) return;
   GP_CUDA(cudaSetDevice(ctx->device));
   while ((int)ctx->workers.size() < workers) {
     cudaStream_t s = nullptr;
@@ -29,19 +31,10 @@ void ensure_batch_workers(gp_ctx *ctx, int workers) {
     }
     ctx->workers.push_back(w);
   }
-  for (int i = 0; i < workers; i++) ctx->workers[(size_t)i]->device_share = workers;
-  // inputs may still be in flight on the caller's stream
-  cudaEvent_t ready;
-  GP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-  GP_CUDA(cudaEventRecord(ready, ctx->stream));
-  for (int i = 0; i < workers; i++) GP_CUDA(cudaStreamWaitEvent(ctx->workers[(size_t)i]->stream, ready, 0));
-  GP_CUDA(cudaEventDestroy(ready));
-}
-
-void batch_per_graph(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx, int workers,
-                     const gp_config &cfg) {
-  if (idx.empty()) return;
-  ensure_batch_workers(ctx, workers);
+  for (int i = 0; i < workers; i++) {
+    ctx->workers[(size_t)i]->device_share = share;
+    GP_CUDA(cudaStreamWaitEvent(ctx->workers[(size_t)i]->stream, ready, 0));
+  }
   std::vector<int32_t> order(idx);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return items[a].g.m2 > items[b].g.m2; });
   std::atomic<size_t> next{0};
@@ -98,10 +91,7 @@ extern "C" gp_status gp_partition_batch(gp_ctx *ctx, gp_batch_item *items, int32
   }
   try {
     GP_CUDA(cudaSetDevice(ctx->device));
-    const gp_batch_tuning &t = gp::batch_tuning(ctx);
-    std::vector<int32_t> rest = valid;
-    if (t.engine && gp::engine_config_ok(c)) rest = gp::engine_run(ctx, items, valid, c, t, nullptr);
-    gp::batch_per_graph(ctx, items, rest, workers, c);
+    gp::batch_run(ctx, items, valid, workers, c, gp::batch_tuning(ctx));
   } catch (const gp::Error &e) {
     ctx->last_error = e.msg;
     return e.status;

@@ -448,15 +448,17 @@ void check_blocks(gp_ctx *ctx, const int32_t *blocks, int n, int k);
 void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, uint64_t seed,
                     const gp_config &cfg, int32_t *blocks, int64_t *cut_out, gp_partition_stats *st);
 
-// Batched form (batch.cu, engine.cu): the worker contexts, the per-graph path
-// over a list of items, the engine over a list of items (returns the items it
-// left to the per-graph path: not taken, or hierarchy too large for its arena).
-void ensure_batch_workers(gp_ctx *ctx, int workers);
+// Batched form (batch.cu, engine.cu).  batch_per_graph: the listed items on
+// `workers` worker contexts (created on first use), each worker's persistent
+// grids limited to 1/share of the device, after `ready` (an event on the
+// caller's stream).  batch_run: the engine for the items it takes, beside the
+// per-graph path for the rest, then the per-graph path for engine items that
+// outgrew their arena.
 void batch_per_graph(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx, int workers,
-                     const gp_config &cfg);
+                     const gp_config &cfg, int share, cudaEvent_t ready);
+void batch_run(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx, int workers,
+               const gp_config &cfg, const gp_batch_tuning &t);
 bool engine_config_ok(const gp_config &cfg);
-std::vector<int32_t> engine_run(gp_ctx *ctx, gp_batch_item *items, const std::vector<int32_t> &idx,
-                                const gp_config &cfg, const gp_batch_tuning &t, double *engine_ms);
 const gp_batch_tuning &batch_tuning(gp_ctx *ctx);
 
 }  // namespace gp

@@ -218,3 +218,18 @@ def test_autotune_installs_a_table_and_results_stay_identical(gp, ctx):
         b1, c1, _ = ctx.gp_partition(dg, k, eps, seed)
         assert cut == c1 and np.array_equal(blocks.cpu().numpy(), b1.cpu().numpy())
     ctx.batch_set_tuning()  # defaults again
+
+
+def test_engine_beside_the_per_graph_path(gp, ctx):
+    """Small items on the engine while the larger ones run on the per-graph path at the same time."""
+    jobs = _mix(48, 5, nmax=60000)
+    dgs = [(gp.DeviceGraph.from_host(g), k, eps, seed) for g, k, eps, seed in jobs]
+    ctx.batch_set_tuning(engine=1, threads=512, max_entries=1 << 15, max_nodes=1 << 24)
+    res = ctx.gp_partition_batch(dgs, workers=4, details=True)
+    flags = [r[2] for r in res]
+    assert 0 < sum(flags) < len(flags), "both paths ran"
+    for (dg, k, eps, seed), (blocks, cut, eng, st) in zip(dgs, res):
+        assert eng == (1 if dg.m2 <= 1 << 15 else 0)
+        b1, c1, _ = ctx.gp_partition(dg, k, eps, seed)
+        assert cut == c1 and np.array_equal(blocks.cpu().numpy(), b1.cpu().numpy())
+    ctx.batch_set_tuning()
