@@ -304,6 +304,256 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
   add_units(a.units, ue, uv, uc, up, a.label8 != nullptr);
 }
 
+// ----------------- degree <= 32 with E entries per lane: G lanes per node
+//
+// The same rating and choice as k_rate_group, with every lane of a G-lane group
+// holding up to E neighbours, so that a warp rates 32/G nodes of degree up to
+// G * E side by side and every group-wide reduction of the choice serves 32/G
+// nodes at once (nodes of degree 9-32 on 8 or 16 lanes instead of a whole warp).
+template <int MODE, int G, int E, int U, int LK>
+__global__ void __launch_bounds__(kThreads, 4) k_rate_multi(RateArgs a) {
+  static_assert(G == 8 || G == 16, "group width");
+  constexpr int NV = 32 / G;
+  constexpr int PER = NV * U;
+  constexpr int TS = 2 * G * E;  // hash-table slots per (set, group)
+  constexpr int TBITS = TS == 32 ? 5 : TS == 64 ? 6 : 7;
+  static_assert((1 << TBITS) == TS, "table size");
+  constexpr int TW = LK == LK_DENSE ? U * NV * kDenseLabels : U * NV * TS;  // table words per warp
+  __shared__ int s_tk[LK == LK_DENSE ? 1 : kWarpsPerBlock][LK == LK_DENSE ? 1 : TW];
+  __shared__ int s_tv[kWarpsPerBlock][TW];
+  constexpr bool kSmemW = MODE == RATE_LP && LK != LK_WIDE;
+  __shared__ int s_w[kSmemW ? 256 : 1];
+  if (a.stop && *a.stop) return;
+  if (kSmemW) {
+    for (int t = threadIdx.x; t < a.wlabels; t += blockDim.x) s_w[t] = a.weight[t];
+    __syncthreads();
+  }
+  const int lane = (int)lane_id(), wib = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane % G;
+  const unsigned gmask = ((1u << G) - 1u) << (grp * G);
+  for (int t = lane; t < TW; t += 32) {
+    if (LK != LK_DENSE) s_tk[wib][t] = -1;
+    s_tv[wib][t] = 0;
+  }
+  __syncwarp();
+  const int begin = a.offs[a.key], end = list_end(a);
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  unsigned long long ue = 0, uv = 0, uc = 0, up = 0;
+  for (int base = begin + wid * PER; base < end; base += nw * PER) {
+    int v[U], st[U], deg[U], own[U], cv[U];
+    int L[U][E], w[U][E], u[U][E];
+    bool skip[U];
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      const int i = base + q * NV + grp;
+      const int4 rec = i < end ? a.list[i] : make_int4(-1, 0, 0, 0);
+      v[q] = rec.x; st[q] = rec.y; deg[q] = rec.z; cv[q] = rec.w;
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      skip[q] = a.dirty && v[q] >= 0 && !a.dirty[v[q]];
+      if (skip[q]) { v[q] = -1; deg[q] = 0; }
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      const bool ok = v[q] >= 0;
+      own[q] = ok ? (LK == LK_WIDE ? a.label[v[q]] : (int)a.label8[v[q]]) : -2;
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++)
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const int j = gl + e * G;
+        const bool ok = j < deg[q];
+        u[q][e] = ok ? __ldcs(a.adjncy + st[q] + j) : -1;  // rows are read once a round: evict first
+        w[q][e] = ok ? __ldcs(a.adjwgt + st[q] + j) : 0;
+      }
+#pragma unroll
+    for (int q = 0; q < U; q++)
+#pragma unroll
+      for (int e = 0; e < E; e++)
+        L[q][e] = u[q][e] >= 0 ? (LK == LK_WIDE ? a.label[u[q][e]] : (int)a.label8[u[q][e]]) : -1;
+    int own_r[U], sum[U][E];
+    bool lead[U][E];
+    if (LK == LK_DENSE) {
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int sb = (q * NV + grp) * kDenseLabels;
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (u[q][e] >= 0) atomicAdd(&s_tv[wib][sb + L[q][e]], w[q][e]);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int sb = (q * NV + grp) * kDenseLabels;
+        own_r[q] = v[q] >= 0 ? s_tv[wib][sb + own[q]] : 0;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+          sum[q][e] = u[q][e] >= 0 ? s_tv[wib][sb + L[q][e]] : 0;
+          lead[q][e] = u[q][e] >= 0;  // duplicates of a label are harmless below
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int sb = (q * NV + grp) * kDenseLabels;
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (u[q][e] >= 0) s_tv[wib][sb + L[q][e]] = 0;
+      }
+      __syncwarp();
+    } else {
+      int slot[U][E];
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        const int sb = (q * NV + grp) * TS;
+        int *tk = &s_tk[wib][sb];
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+          slot[q][e] = -1;
+          lead[q][e] = false;
+          if (u[q][e] < 0) continue;
+          unsigned sl = ((unsigned)L[q][e] * 2654435761u) >> (32 - TBITS);
+          for (int p = 0; p < TS; p++) {  // bounded: a group holds at most G E labels in 2 G E slots
+            const int prev = atomicCAS(&tk[sl], -1, L[q][e]);
+            if (prev == -1) { lead[q][e] = true; break; }
+            if (prev == L[q][e]) break;
+            sl = (sl + 1) & (TS - 1);
+          }
+          slot[q][e] = sb + (int)sl;
+          atomicAdd(&s_tv[wib][slot[q][e]], w[q][e]);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++)
+#pragma unroll
+        for (int e = 0; e < E; e++) sum[q][e] = slot[q][e] >= 0 ? s_tv[wib][slot[q][e]] : 0;
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++)
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (lead[q][e]) { s_tk[wib][slot[q][e]] = -1; s_tv[wib][slot[q][e]] = 0; }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        unsigned o = 0;
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (lead[q][e] && L[q][e] == own[q]) o = max(o, (unsigned)sum[q][e]);
+        own_r[q] = (int)__reduce_max_sync(gmask, o);
+      }
+    }
+    // choose (as k_rate_group): all U sets advance together; a group whose leading candidate does
+    // not fit reads the weights of all its remaining candidates on the next pass
+    bool alive[U][E], searching[U], eager[U];
+    unsigned best[U];
+    if (a.dirty) {
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        unsigned ra = 0;
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (lead[q][e] && L[q][e] != own[q]) ra = max(ra, (unsigned)sum[q][e]);
+        const int rall = (int)__reduce_max_sync(gmask, ra);
+        if (gl == 0 && v[q] >= 0 && rall <= own_r[q]) a.dirty[v[q]] = 0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        alive[q][e] = lead[q][e] && L[q][e] != own[q];
+        uc += alive[q][e];
+        if (kSmemW && alive[q][e]) alive[q][e] = (int64_t)s_w[L[q][e]] + cv[q] <= a.bound;
+      }
+      searching[q] = v[q] >= 0;
+      eager[q] = kSmemW;
+      best[q] = 0xFFFFFFFFu;
+    }
+    for (int it = 0; it <= G * E; it++) {  // bounded: every pass drops one candidate per searching group
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < U; q++) any = any || searching[q];
+      if (!__any_sync(FULL, any)) break;
+      if (MODE == RATE_LP && !kSmemW) {
+#pragma unroll
+        for (int q = 0; q < U; q++)
+#pragma unroll
+          for (int e = 0; e < E; e++)
+            if (eager[q] && searching[q] && alive[q][e] && (int64_t)a.weight[L[q][e]] + cv[q] > a.bound)
+              alive[q][e] = false;
+      }
+      unsigned c[U];
+      bool holder[U];
+#pragma unroll
+      for (int q = 0; q < U; q++) {
+        int rl = -1;
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (searching[q] && alive[q][e]) rl = max(rl, sum[q][e]);
+        const int r = __reduce_max_sync(gmask, rl);
+        if (r < 0 || (MODE == RATE_LP && r <= own_r[q])) searching[q] = false;
+        unsigned h[E], hl = 0xFFFFFFFFu;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+          const bool top = searching[q] && alive[q][e] && sum[q][e] == r;
+          h[e] = top ? h32(a.ktie, (uint32_t)v[q], (uint32_t)L[q][e]) : 0xFFFFFFFFu;
+          hl = min(hl, h[e]);
+        }
+        const unsigned hmin = __reduce_min_sync(gmask, hl);
+        unsigned cl = 0xFFFFFFFFu;
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          if (searching[q] && alive[q][e] && sum[q][e] == r && h[e] == hmin) cl = min(cl, (unsigned)L[q][e]);
+        c[q] = __reduce_min_sync(gmask, cl);
+        holder[q] = false;
+#pragma unroll
+        for (int e = 0; e < E; e++)
+          holder[q] = holder[q] || (searching[q] && alive[q][e] && sum[q][e] == r && h[e] == hmin &&
+                                    (unsigned)L[q][e] == c[q]);
+      }
+      if (MODE != RATE_LP || kSmemW) {
+#pragma unroll
+        for (int q = 0; q < U; q++)
+          if (searching[q]) { best[q] = c[q]; searching[q] = false; }
+      } else {
+        int wc[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) wc[q] = (holder[q] && !eager[q]) ? a.weight[c[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+          // after an eager pass every remaining candidate fits
+          const unsigned fits = holder[q] && (eager[q] || (int64_t)wc[q] + cv[q] <= a.bound) ? 1u : 0u;
+          if (__reduce_or_sync(gmask, fits) && searching[q]) { best[q] = c[q]; searching[q] = false; }
+#pragma unroll
+          for (int e = 0; e < E; e++) alive[q][e] = alive[q][e] && (unsigned)L[q][e] != c[q];
+          eager[q] = true;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      if (gl == 0 && v[q] >= 0) {
+        ue += deg[q];
+        uv += 1;
+        if (best[q] != 0xFFFFFFFFu) {
+          emit<MODE>(a, base + q * NV + grp, v[q], (int)best[q], cv[q], own[q]);
+          up += 1;
+        } else if (MODE == RATE_LP) {
+          a.prop[base + q * NV + grp] = make_int2(-1, 0);
+        }
+      } else if (gl == 0 && skip[q] && MODE == RATE_LP) {
+        a.prop[base + q * NV + grp] = make_int2(-1, 0);
+      }
+    }
+  }
+  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr);
+}
+
 // --------------------------------------- degree <= 128: warp/node + table
 
 template <int MODE>
@@ -573,9 +823,12 @@ __global__ void __launch_bounds__(kThreads) k_compact_dirty(const int4 *list, co
                                                             const uint8_t *dirty, int4 *clist, int32_t *ccount,
                                                             const int *stop) {
   if (stop && *stop) return;
+  __shared__ int s_cnt[kNumBuckets], s_base[kNumBuckets];
   const int begin = offs[k0], end = offs[k1];
   const int lane = (int)lane_id();
   for (int base = begin + (int)(blockIdx.x * blockDim.x); base < end; base += gridDim.x * blockDim.x) {
+    if (threadIdx.x < kNumBuckets) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
     const int i = base + (int)threadIdx.x;
     int bk = k1;  // bucket of the position (k1 past the end)
     int b = -1;   // bucket if the record is kept
@@ -597,18 +850,21 @@ __global__ void __launch_bounds__(kThreads) k_compact_dirty(const int4 *list, co
     const unsigned run_hi = after ? (unsigned)__ffs(after) - 1 : 32u;  // one past the run
     const unsigned run = (run_hi == 32 ? FULL : ((1u << run_hi) - 1u)) & ~((1u << run_lo) - 1u);
     const unsigned peers = kept & run;
+    int pos = 0;
     if (b >= 0) {
+      // the block's kept records of each bucket are counted in shared memory, and the bucket's
+      // global cursor advances once per block and bucket
       const int leader = __ffs(peers) - 1;
-      int pos = 0;
-      if (lane == leader) pos = atomicAdd(&ccount[b], __popc(peers));
-      pos = __shfl_sync(peers, pos, leader);
-      clist[offs[b] + pos + __popc(peers & lanemask_lt())] = rec;
+      if (lane == leader) pos = atomicAdd(&s_cnt[b - k0], __popc(peers));
+      pos = __shfl_sync(peers, pos, leader) + __popc(peers & lanemask_lt());
     }
+    __syncthreads();
+    if (threadIdx.x < kNumBuckets && s_cnt[threadIdx.x] > 0)
+      s_base[threadIdx.x] = atomicAdd(&ccount[k0 + threadIdx.x], s_cnt[threadIdx.x]);
+    __syncthreads();
+    if (b >= 0) clist[offs[b] + s_base[b - k0] + pos] = rec;
   }
 }
-
-// Every applied move makes its node and the node's neighbours dirty (a warp
-// takes two moves at a time and reads both rows side by side).
 __global__ void __launch_bounds__(kThreads) k_mark_dirty(const int4 *mov, int nmov, const uint64_t *ov_key,
                                                          const uint32_t *ov_val, const uint8_t *ov_acc, int nov,
                                                          const uint64_t *cutoff, uint64_t kprio,
@@ -1225,14 +1481,14 @@ void launch_groups(gp_ctx *ctx, const RateArgs &a0, int bucket_key_base, const i
   }
   if (!hcnt || hcnt[1] > 0) {
     a.key = bucket_key_base + 1;
-    k_rate_group<MODE, 16, 2, LK><<<rate_grid(ctx, hcnt ? hcnt[1] : -1, group_nodes_per_block<16, 2>(), cap),
-                                    kThreads, 0, ctx->stream>>>(a);
+    k_rate_multi<MODE, 8, 2, 2, LK><<<rate_grid(ctx, hcnt ? hcnt[1] : -1, group_nodes_per_block<8, 2>(), cap),
+                                      kThreads, 0, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
   }
   if (!hcnt || hcnt[2] > 0) {
     a.key = bucket_key_base + 2;
-    k_rate_group<MODE, 32, 4, LK><<<rate_grid(ctx, hcnt ? hcnt[2] : -1, group_nodes_per_block<32, 4>(), cap),
-                                    kThreads, 0, ctx->stream>>>(a);
+    k_rate_multi<MODE, 16, 2, 2, LK><<<rate_grid(ctx, hcnt ? hcnt[2] : -1, group_nodes_per_block<16, 2>(), cap),
+                                       kThreads, 0, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
   }
 }
@@ -1370,7 +1626,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       a.stop = &C->stop; a.units = units_rate; a.label8 = label8;
       a.wlabels = label8 ? (int)nlabels : 0;
       a.dirty = dirty.get();
-      if (use_dirty) {
+      if (use_dirty && r > 0) {  // in round 0 every node is still marked: the lists stay as they are
         const int k0c = s * kNumBuckets;
         GP_CUDA(cudaMemsetAsync(ccount.get() + k0c, 0, sizeof(int32_t) * kNumBuckets, ctx->stream));
         const int act = hoffs[k0c + kNumBuckets] - hoffs[k0c];
@@ -1393,8 +1649,8 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
       {
         ProfScope ps(ctx, p.prof_accept);
         k_decide<<<grid_for(active, kThreads, grid), kThreads, 0, ctx->stream>>>(
-            use_dirty ? clist.get() : list.get(), offs.get(), k0, k1, prop.get(), weight, incoming.get(), p.bound,
-            mov.get(), ov_key.get(), ov_val.get(), C, kprio, use_dirty ? ccount.get() : nullptr);
+            use_dirty && r > 0 ? clist.get() : list.get(), offs.get(), k0, k1, prop.get(), weight, incoming.get(),
+            p.bound, mov.get(), ov_key.get(), ov_val.get(), C, kprio, use_dirty && r > 0 ? ccount.get() : nullptr);
         GP_LAUNCH_CHECK();
       }
       Counters hdr;
