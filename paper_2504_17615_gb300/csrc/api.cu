@@ -346,13 +346,14 @@ gp_status gp_profile_read(gp_ctx *ctx, int i, int64_t *launches, double *ms, dou
         // labels are one byte); per candidate label its weight (4 B); per node
         // offsets, weight, own label (16 B); per proposal target write + incoming
         // update (12 B)
-        b = 12.0 * u[0] - 3.0 * u[4] + 4.0 * u[2] + 16.0 * u[1] + 12.0 * u[3];
+        // (the weight is not read on unit-weight inputs)
+        b = 12.0 * u[0] - 3.0 * u[4] - 4.0 * u[5] + 4.0 * u[2] + 16.0 * u[1] + 12.0 * u[3];
         break;
       case gp::PROF_CONTRACT:
         // map: per fine entry neighbour id, weight, coarse id of the neighbour read (12 B) and
         // (coarse neighbour, weight) written to the segment (8 B); merge: every segment entry
         // read (8 B), every merged entry written (8 B)
-        b = 28.0 * u[0] + 8.0 * u[3];
+        b = 28.0 * u[0] - 4.0 * u[5] + 8.0 * u[3];
         break;
       default:
         b = ctx->prof_host_bytes[i];

@@ -27,7 +27,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kWarpSlots = 256;
 constexpr int kWarpMaxUb = 128;
 constexpr int kBlockSmemSlots = 4096;
-constexpr int kMapUnroll = 4;
+constexpr int kMapUnroll = 8;
 
 __device__ __forceinline__ unsigned slot_hash(int B, int bits) {
   return ((unsigned)B * 2654435761u) >> (32 - bits);
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_map(const int32_t *xadj, const int
     const int last = (int)((n - u0) < 32 ? (n - u0) : 32) - 1;
     const int e1 = __shfl_sync(FULL, xe, last);
     if (lane == 0) ue += (unsigned long long)(e1 - e0);
-    // four entries per lane in flight: ids, then coarse ids, then the writes
+    // kMapUnroll entries per lane in flight: ids, then coarse ids, then the writes
     for (int f0 = e0; f0 < e1; f0 += 32 * kMapUnroll) {
       int e[kMapUnroll], bj[kMapUnroll], Aj[kMapUnroll], nb[kMapUnroll];
 #pragma unroll
@@ -105,11 +105,14 @@ __global__ void __launch_bounds__(kThreads) k_map(const int32_t *xadj, const int
       for (int r = 0; r < kMapUnroll; r++) nb[r] = e[r] < e1 ? cmap[nb[r]] : 0;
 #pragma unroll
       for (int r = 0; r < kMapUnroll; r++)
-        if (e[r] < e1) temp[bj[r] + e[r]] = nb[r] == Aj[r] ? make_int2(-1, 0) : make_int2(nb[r], __ldcs(adjwgt + e[r]));
+        if (e[r] < e1) temp[bj[r] + e[r]] = nb[r] == Aj[r] ? make_int2(-1, 0) : make_int2(nb[r], adjwgt ? __ldcs(adjwgt + e[r]) : 1);
     }
   }
   ue = warp_sum(ue);
-  if (units && lane == 0) atomicAdd(units + 0, ue);
+  if (units && lane == 0) {
+    atomicAdd(units + 0, ue);
+    if (!adjwgt) atomicAdd(units + 5, ue);
+  }
 }
 
 struct MergeArgs {
@@ -280,7 +283,7 @@ void contract_graph(gp_ctx *ctx, const DevGraph &g, const int32_t *cmap, int32_t
     ProfScope ps(ctx, PROF_CONTRACT);
     if (n > 0) {
       k_map<<<grid_for((int64_t)n, kThreads, ctx->num_sms * 16), kThreads, 0, ctx->stream>>>(
-          g.xadj, g.adjncy, g.adjwgt, cmap, moff.get(), tstart.get(), n, temp.get(), units);
+          g.xadj, g.adjncy, g.unit_w ? nullptr : g.adjwgt, cmap, moff.get(), tstart.get(), n, temp.get(), units);
       GP_LAUNCH_CHECK();
     }
     k_merge_warp<<<grid_for((int64_t)nc * 32, kThreads, ctx->num_sms * 8), kThreads, 0, ctx->stream>>>(a);

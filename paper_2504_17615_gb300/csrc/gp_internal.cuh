@@ -81,8 +81,9 @@ enum ProfClass {
 };
 
 // device-side unit counters, per class: [0] entries, [1] vertices, [2] candidates, [3] proposals,
-// [4] entries whose neighbour label was read as one byte
-constexpr int PROF_UNITS = 5;
+// [4] entries whose neighbour label was read as one byte, [5] entries whose weight was not read
+// (unit edge weights)
+constexpr int PROF_UNITS = 6;
 
 struct ProfRecord {
   int cls;
@@ -382,6 +383,9 @@ struct DevGraph {
   int32_t n = 0;
   int64_t m2 = 0;
   int32_t *xadj = nullptr, *adjncy = nullptr, *vwgt = nullptr, *adjwgt = nullptr;
+  // every edge weight is 1 (found by the input validation: positive weights summing to the
+  // entry count); kernels that honour it use 1 instead of reading adjwgt
+  bool unit_w = false;
   // ownership (when created by the library)
   DBuf<int32_t> bx, ba, bv, bw;
   gp_graph view() const {
@@ -439,6 +443,7 @@ void cut_and_weights(gp_ctx *ctx, const DevGraph &g, const int32_t *blocks, int3
 struct GraphTotals {
   int64_t W;
   int64_t cmax;
+  bool unit_w;  // every edge weight is 1
 };
 GraphTotals validate_graph(gp_ctx *ctx, const DevGraph &g, bool full);
 int64_t lmax_of(int64_t W, int32_t k, int64_t eps_ppm);

@@ -55,12 +55,13 @@ __device__ __forceinline__ int list_end(const RateArgs &a) {
 
 __device__ __forceinline__ void add_units(unsigned long long *units, unsigned long long e,
                                           unsigned long long v, unsigned long long c,
-                                          unsigned long long p, bool narrow) {
+                                          unsigned long long p, bool narrow, bool implied) {
   if (!units) return;
   e = warp_sum(e); v = warp_sum(v); c = warp_sum(c); p = warp_sum(p);
   if (lane_id() == 0) {
     if (e) atomicAdd(units + 0, e);
     if (e && narrow) atomicAdd(units + 4, e);
+    if (e && implied) atomicAdd(units + 5, e);
     if (v) atomicAdd(units + 1, v);
     if (c) atomicAdd(units + 2, c);
     if (p) atomicAdd(units + 3, p);
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
     for (int q = 0; q < U; q++) {
       const bool ok = gl < deg[q];
       u[q] = ok ? __ldcs(a.adjncy + st[q] + gl) : -1;  // rows are read once a round: evict first
-      w[q] = ok ? __ldcs(a.adjwgt + st[q] + gl) : 0;
+      w[q] = ok ? (a.adjwgt ? __ldcs(a.adjwgt + st[q] + gl) : 1) : 0;
     }
 #pragma unroll
     for (int q = 0; q < U; q++)
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
       }
     }
   }
-  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr);
+  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr, a.adjwgt == nullptr);
 }
 
 // ----------------- degree <= 32 with E entries per lane: G lanes per node
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rate_multi(RateArgs a) {
         const int j = gl + e * G;
         const bool ok = j < deg[q];
         u[q][e] = ok ? __ldcs(a.adjncy + st[q] + j) : -1;  // rows are read once a round: evict first
-        w[q][e] = ok ? __ldcs(a.adjwgt + st[q] + j) : 0;
+        w[q][e] = ok ? (a.adjwgt ? __ldcs(a.adjwgt + st[q] + j) : 1) : 0;
       }
 #pragma unroll
     for (int q = 0; q < U; q++)
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rate_multi(RateArgs a) {
       }
     }
   }
-  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr);
+  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr, a.adjwgt == nullptr);
 }
 
 // --------------------------------------- degree <= 128: warp/node + table
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
     const int own = label_of(a, v);
     for (int j = lane; j < deg; j += 32) {
       const int L = label_of(a, __ldcs(a.adjncy + start + j));
-      const int w = __ldcs(a.adjwgt + start + j);
+      const int w = a.adjwgt ? __ldcs(a.adjwgt + start + j) : 1;
       unsigned s = slot_hash(L, 8);
       for (int probe = 0; probe < kMedSlots; probe++) {  // bounded: the table never fills
         const int prev = atomicCAS(&tk[s], -1, L);
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_medium(RateArgs a) {
     for (int t = lane; t < kMedSlots; t += 32) { tk[t] = -1; tv[t] = 0; }
     __syncwarp();
   }
-  add_units(a.units, ue * (lane == 0), uv * (lane == 0), uc, up, a.label8 != nullptr);
+  add_units(a.units, ue * (lane == 0), uv * (lane == 0), uc, up, a.label8 != nullptr, a.adjwgt == nullptr);
 }
 
 // --------------------------------------------- degree > 128: block/node
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
     int *tv = in_smem ? s_v : gv;
     for (int j = threadIdx.x; j < deg; j += blockDim.x) {
       const int L = label_of(a, __ldcs(a.adjncy + start + j));
-      const int w = __ldcs(a.adjwgt + start + j);
+      const int w = a.adjwgt ? __ldcs(a.adjwgt + start + j) : 1;
       unsigned s = slot_hash(L, bits);
       for (int probe = 0; probe < tsize; probe++) {  // bounded: the table never fills
         const int prev = atomicCAS(&tk[s], -1, L);
@@ -722,7 +723,7 @@ __global__ void __launch_bounds__(kThreads) k_rate_large(RateArgs a) {
     for (int t = threadIdx.x; t < tsize; t += blockDim.x) { tk[t] = -1; tv[t] = 0; }
     __syncthreads();
   }
-  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr);
+  add_units(a.units, ue, uv, uc, up, a.label8 != nullptr, a.adjwgt == nullptr);
 }
 
 // ----------------------------------------------------- per-round buckets
@@ -1487,7 +1488,7 @@ void launch_groups(gp_ctx *ctx, const RateArgs &a0, int bucket_key_base, const i
   }
   if (!hcnt || hcnt[2] > 0) {
     a.key = bucket_key_base + 2;
-    k_rate_multi<MODE, 16, 2, 2, LK><<<rate_grid(ctx, hcnt ? hcnt[2] : -1, group_nodes_per_block<16, 2>(), cap),
+    k_rate_multi<MODE, 16, 2, 3, LK><<<rate_grid(ctx, hcnt ? hcnt[2] : -1, group_nodes_per_block<16, 3>(), cap),
                                        kThreads, 0, ctx->stream>>>(a);
     GP_LAUNCH_CHECK();
   }
@@ -1620,7 +1621,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
     for (int s = 0; s < S; s++) {
       if (p.dbg_max_subrounds >= 0 && subs >= p.dbg_max_subrounds) { stop = true; break; }
       RateArgs a{};
-      a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
+      a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.unit_w ? nullptr : g.adjwgt; a.vwgt = g.vwgt;
       a.label = label; a.weight = weight; a.list = list.get(); a.offs = offs.get();
       a.bound = p.bound; a.ktie = ktie; a.prop = prop.get(); a.incoming = incoming.get();
       a.stop = &C->stop; a.units = units_rate; a.label8 = label8;
@@ -1816,7 +1817,7 @@ void favourites_bucketed(gp_ctx *ctx, const DevGraph &g, const int32_t *label, c
   RateTables tables;
   make_tables(ctx, g, tables);
   RateArgs a{};
-  a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.adjwgt; a.vwgt = g.vwgt;
+  a.xadj = g.xadj; a.adjncy = g.adjncy; a.adjwgt = g.unit_w ? nullptr : g.adjwgt; a.vwgt = g.vwgt;
   a.label = label; a.weight = nullptr; a.list = list.get(); a.offs = offs.get();
   a.bound = U; a.ktie = kfav; a.fav_keys = keys.get(); a.stop = nullptr;
   launch_rate<RATE_FAV>(ctx, a, 0, tables, 0, nullptr);

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) k_cut(const int32_t *xadj, const int32_t 
       for (int r = 0; r < R; r++) {
         const bool in = e[r] < e1;
         v[r] = in ? __ldcs(adjncy + e[r]) : 0;
-        w[r] = in ? __ldcs(adjwgt + e[r]) : 0;
+        w[r] = in ? (adjwgt ? __ldcs(adjwgt + e[r]) : 1) : 0;
       }
 #pragma unroll
       for (int r = 0; r < R; r++)
@@ -226,7 +226,7 @@ GraphTotals validate_graph(gp_ctx *ctx, const DevGraph &g, bool full) {
   GP_REQUIRE(g.m2 >= 0 && g.m2 < ((int64_t)1 << 31), GP_ERR_INVALID, "m2 must be in [0, 2^31)");
   GP_REQUIRE(g.n == 0 || (g.xadj && g.vwgt), GP_ERR_INVALID, "null graph arrays");
   GP_REQUIRE(g.m2 == 0 || (g.adjncy && g.adjwgt), GP_ERR_INVALID, "null graph arrays");
-  if (g.n == 0) return GraphTotals{0, 0};
+  if (g.n == 0) return GraphTotals{0, 0, false};
   DBuf<ValOut> o(ctx, 1);
   o.zero();
   k_validate_nodes<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(g.xadj, g.vwgt, g.n, g.m2,
@@ -251,7 +251,8 @@ GraphTotals validate_graph(gp_ctx *ctx, const DevGraph &g, bool full) {
       GP_REQUIRE(h.nlo == h.nhi && h.hlo == h.hhi, GP_ERR_INVALID, "graph is not symmetric");
     GP_REQUIRE(h.wsum / 2 <= 0x7FFFFFFFull, GP_ERR_OVERFLOW, "total edge weight exceeds 2^31 - 1");
   }
-  return GraphTotals{(int64_t)h.csum, (int64_t)h.cmax};
+  // all weights are >= 1, so a total equal to the entry count means all are 1
+  return GraphTotals{(int64_t)h.csum, (int64_t)h.cmax, g.m2 > 0 && (int64_t)h.wsum == g.m2};
 }
 
 void project(gp_ctx *ctx, int32_t n, const int32_t *cmap, const int32_t *coarse, int32_t *fine) {
@@ -273,16 +274,18 @@ void cut_and_weights(gp_ctx *ctx, const DevGraph &g, const int32_t *blocks, int3
       DBuf<uint8_t> b8(ctx, (size_t)g.n);
       k_narrow<<<grid_for(g.n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(blocks, g.n, b8.get());
       GP_LAUNCH_CHECK();
-      k_cut<uint8_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, b8.get(), g.n, c.get());
+      k_cut<uint8_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.unit_w ? nullptr : g.adjwgt, b8.get(),
+                                                    g.n, c.get());
       GP_LAUNCH_CHECK();
     } else {
-      k_cut<int32_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.adjwgt, blocks, g.n, c.get());
+      k_cut<int32_t><<<grid, 256, 0, ctx->stream>>>(g.xadj, g.adjncy, g.unit_w ? nullptr : g.adjwgt, blocks,
+                                                    g.n, c.get());
       GP_LAUNCH_CHECK();
     }
   }
   // per entry: neighbour id, weight, neighbour block; per node: row offset, own block
   const double bb = k <= 255 ? 1.0 : 4.0;
-  prof_bytes(ctx, PROF_CUT, (8.0 + bb) * g.m2 + (4.0 + bb) * g.n);
+  prof_bytes(ctx, PROF_CUT, ((g.unit_w ? 4.0 : 8.0) + bb) * g.m2 + (4.0 + bb) * g.n);
   if (bw_host) {
     DBuf<unsigned long long> bw(ctx, (size_t)k);
     block_weights_dev(ctx, g, blocks, k, bw.get());
@@ -384,6 +387,7 @@ void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, u
   std::vector<std::unique_ptr<DevGraph>> G;
   std::vector<DBuf<int32_t>> C;
   G.push_back(std::make_unique<DevGraph>(DevGraph::wrap(input.view())));
+  G[0]->unit_w = tot.unit_w;
   int L = 0;
   while ((int64_t)G[L]->n > (int64_t)cfg.coarsest_factor * k && L < cfg.max_levels) {
     const DevGraph &cur = *G[L];
@@ -454,7 +458,7 @@ void partition_impl(gp_ctx *ctx, const DevGraph &input, int32_t k, double eps, u
   if (L == 0)
     GP_CUDA(cudaMemcpyAsync(blocks, blk.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   int64_t cut = 0;
-  cut_and_weights(ctx, input, blocks, k, &cut, nullptr);
+  cut_and_weights(ctx, *G[0], blocks, k, &cut, nullptr);
   tm.mark(3);
   GP_CUDA(cudaEventSynchronize(tm.ev[3]));
   S.cut = cut;
