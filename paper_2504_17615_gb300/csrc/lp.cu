@@ -912,7 +912,7 @@ struct Counters {
   long long moved_sub;
   long long moved_round;
   long long moved_total;
-  long long nonempty;   // labels of positive weight, counted after the sub-round's moves
+  long long nonempty;   // clustering: change of the number of labels of positive weight in the sub-round
   long long nclusters;
 };
 
@@ -1236,6 +1236,7 @@ struct ApplyArgs {
   Counters *cnt;
   const uint64_t *cutoff;  // 2.5x cap: only moves with key (h32(PRIO), v) below *cutoff apply (null: all)
   uint64_t kprio;
+  int track;  // clustering: count the labels whose weight reaches or leaves 0
 };
 
 __device__ __forceinline__ uint64_t move_key(uint64_t kprio, int v) {
@@ -1261,7 +1262,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
   for (int t = threadIdx.x; t < a.nshared; t += blockDim.x) s_dw[t] = 0;
   if (a.nshared) __syncthreads();
   const int total = a.nmov + a.nov;
-  long long moved = 0;
+  long long moved = 0, dne = 0;  // dne: labels whose weight left 0 minus labels whose weight reached 0
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     int v, K, own, c;
     bool mv;
@@ -1275,8 +1276,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
         atomicAdd(&s_dw[K], c);
         atomicSub(&s_dw[own], c);
       } else {
-        atomicAdd(&a.weight[K], c);
-        atomicSub(&a.weight[own], c);
+        // every update's transition 0 <-> non-0 counted: their sum is the net change
+        const int ok = atomicAdd(&a.weight[K], c);
+        const int oo = atomicSub(&a.weight[own], c);
+        if (a.track) dne += (ok == 0 ? 1 : 0) - (oo == c ? 1 : 0);
       }
       moved++;
     }
@@ -1284,11 +1287,16 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs a) {
   if (a.nshared) {
     __syncthreads();
     for (int t = threadIdx.x; t < a.nshared; t += blockDim.x)
-      if (s_dw[t]) atomicAdd(&a.weight[t], s_dw[t]);
+      if (s_dw[t]) {
+        const int o = atomicAdd(&a.weight[t], s_dw[t]);
+        if (a.track) dne += ((o + s_dw[t] > 0) ? 1 : 0) - ((o > 0) ? 1 : 0);
+      }
   }
   moved = warp_sum(moved);
+  dne = warp_sum(dne);
   if (lane_id() == 0 && moved)
     atomicAdd((unsigned long long *)&a.cnt->moved_sub, (unsigned long long)moved);
+  if (lane_id() == 0 && dne) atomicAdd((unsigned long long *)&a.cnt->nonempty, (unsigned long long)dne);
 }
 
 // ------------------------------------------------------- the 2.5x cap
@@ -1367,20 +1375,6 @@ __global__ void __launch_bounds__(kThreads) k_close(ApplyArgs a, int64_t count_l
     const int K = t < a.nmov ? a.mov[t].y : (int)(a.ov_key[t - a.nmov] >> 32);
     a.incoming[K] = 0;
   }
-  if (count_labels > 0) {
-    long long c = 0;
-    const int4 *w4 = reinterpret_cast<const int4 *>(a.weight);
-    const int64_t n4 = count_labels / 4;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-      const int4 x = w4[i];
-      c += (x.x > 0) + (x.y > 0) + (x.z > 0) + (x.w > 0);
-    }
-    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count_labels;
-         i += (int64_t)gridDim.x * blockDim.x)
-      c += a.weight[i] > 0;
-    c = warp_sum(c);
-    if (lane_id() == 0 && c) atomicAdd((unsigned long long *)&cnt->nonempty, (unsigned long long)c);
-  }
   __syncthreads();
   __shared__ bool s_last;
   if (threadIdx.x == 0) {
@@ -1391,7 +1385,7 @@ __global__ void __launch_bounds__(kThreads) k_close(ApplyArgs a, int64_t count_l
   if (!s_last || threadIdx.x != 0) return;
   __threadfence();
   volatile Counters *vc = cnt;
-  if (count_labels > 0) vc->nclusters = vc->nonempty;
+  if (count_labels > 0) vc->nclusters = vc->nclusters + vc->nonempty;  // k_apply's net change
   vc->nonempty = 0;
   const long long moved = vc->moved_sub;
   vc->moved_round = vc->moved_round + moved;
@@ -1713,6 +1707,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
         aa.weight = weight; aa.incoming = incoming.get(); aa.label8 = label8;
         aa.nshared = agg ? (int)nlabels : 0; aa.cnt = C;
         aa.kprio = kprio;
+        aa.track = p.count_clusters ? 1 : 0;
 
         const int ga = grid_for((int64_t)nmov + nov, kThreads, grid);
         // the 2.5x cap: only when the accepted moves could empty more than D clusters
@@ -1752,7 +1747,7 @@ LpResult lp_run(gp_ctx *ctx, const DevGraph &g, int32_t *label, int32_t *weight,
           }
         }
         const int64_t count_labels = p.count_clusters ? nlabels : 0;
-        const int gc = grid_for(std::max<int64_t>((int64_t)nmov + nov, count_labels / 4), kThreads, grid);
+        const int gc = grid_for((int64_t)nmov + nov, kThreads, grid);
         k_close<<<gc, kThreads, 0, ctx->stream>>>(aa, count_labels, (long long)p.n_min, s == S - 1 ? 1 : 0,
                                                   done.get());
         GP_LAUNCH_CHECK();
