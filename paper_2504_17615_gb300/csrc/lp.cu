@@ -226,20 +226,21 @@ __global__ void __launch_bounds__(kThreads, G == 32 ? 4 : 5) k_rate_group(RateAr
     // node takes at most three passes.
     bool alive[U], searching[U], eager[U];
     unsigned best[U];
-    if (a.dirty) {
+    // no label rated above the own one, admissible or not: the node proposes nothing (so it skips
+    // the choice), and in refinement it stays clean until a neighbour moves
+    bool stay[U];
 #pragma unroll
-      for (int q = 0; q < U; q++) {
-        // no label rated above the own one, admissible or not: clean until a neighbour moves
-        const int rall = (int)__reduce_max_sync(gmask, (lead[q] && L[q] != own[q]) ? (unsigned)sum[q] : 0u);
-        if (gl == 0 && v[q] >= 0 && rall <= own_r[q]) a.dirty[v[q]] = 0;
-      }
+    for (int q = 0; q < U; q++) {
+      const int rall = (int)__reduce_max_sync(gmask, (lead[q] && L[q] != own[q]) ? (unsigned)sum[q] : 0u);
+      stay[q] = MODE == RATE_LP && rall <= own_r[q];
+      if (a.dirty && gl == 0 && v[q] >= 0 && stay[q]) a.dirty[v[q]] = 0;
     }
 #pragma unroll
     for (int q = 0; q < U; q++) {
       alive[q] = lead[q] && L[q] != own[q];
       uc += alive[q];
       if (kSmemW && alive[q]) alive[q] = (int64_t)s_w[L[q]] + cv[q] <= a.bound;
-      searching[q] = v[q] >= 0;
+      searching[q] = v[q] >= 0 && !stay[q];
       eager[q] = kSmemW;
       best[q] = 0xFFFFFFFFu;
     }
@@ -452,16 +453,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_rate_multi(RateArgs a) {
     // not fit reads the weights of all its remaining candidates on the next pass
     bool alive[U][E], searching[U], eager[U];
     unsigned best[U];
-    if (a.dirty) {
+    // no label rated above the own one, admissible or not: the node proposes nothing (so it skips
+    // the choice), and in refinement it stays clean until a neighbour moves
+    bool stay[U];
 #pragma unroll
-      for (int q = 0; q < U; q++) {
-        unsigned ra = 0;
+    for (int q = 0; q < U; q++) {
+      unsigned ra = 0;
 #pragma unroll
-        for (int e = 0; e < E; e++)
-          if (lead[q][e] && L[q][e] != own[q]) ra = max(ra, (unsigned)sum[q][e]);
-        const int rall = (int)__reduce_max_sync(gmask, ra);
-        if (gl == 0 && v[q] >= 0 && rall <= own_r[q]) a.dirty[v[q]] = 0;
-      }
+      for (int e = 0; e < E; e++)
+        if (lead[q][e] && L[q][e] != own[q]) ra = max(ra, (unsigned)sum[q][e]);
+      const int rall = (int)__reduce_max_sync(gmask, ra);
+      stay[q] = MODE == RATE_LP && rall <= own_r[q];
+      if (a.dirty && gl == 0 && v[q] >= 0 && stay[q]) a.dirty[v[q]] = 0;
     }
 #pragma unroll
     for (int q = 0; q < U; q++) {
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rate_multi(RateArgs a) {
         uc += alive[q][e];
         if (kSmemW && alive[q][e]) alive[q][e] = (int64_t)s_w[L[q][e]] + cv[q] <= a.bound;
       }
-      searching[q] = v[q] >= 0;
+      searching[q] = v[q] >= 0 && !stay[q];
       eager[q] = kSmemW;
       best[q] = 0xFFFFFFFFu;
     }

@@ -101,7 +101,8 @@ __device__ __forceinline__ unsigned rate_group(const int32_t *__restrict__ adjnc
     ncand += alive[e] ? 1 : 0;
     if (!FAV && s_wl && alive[e]) alive[e] = (int64_t)s_wl[L[e]] + cv <= bound;
   }
-  bool eager = FAV || s_wl != nullptr, searching = v >= 0;
+  // no label rated above own (admissible or not): nothing to propose, the choice is skipped
+  bool eager = FAV || s_wl != nullptr, searching = v >= 0 && (FAV || !stable);
   unsigned best = 0xFFFFFFFFu;
   for (int it = 0; it < 3; it++) {  // lazy pass, eager pass, one to find nothing left
     if (!__any_sync(0xFFFFFFFFu, searching)) break;
