@@ -70,3 +70,40 @@ def test_no_cpu_fallback_in_the_package():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "gp_oracle" not in text, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes records of the binding have the C layout of include/gp.h (sizes and the offsets
+    of the fields the batched form and the partition statistics hand back)."""
+    import shutil
+    import subprocess
+    import paper_2504_17615_gb300 as gp
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    checks = {
+        "gp_graph": ["n", "m2", "adjwgt"],
+        "gp_config": ["tau_e_num", "small_lp_nodes"],
+        "gp_level_stats": ["m_hat", "threshold", "clusters_final"],
+        "gp_partition_stats": ["lv", "U", "n_coarsest", "ms_total"],
+        "gp_batch_item": ["g", "eps", "blocks", "cut", "status", "engine", "stats"],
+        "gp_batch_tuning": ["threads", "max_entries", "arena_bytes", "class_entries", "class_items",
+                            "class_threads", "class_engine_gps", "class_path_gps", "tune_ms"],
+        "gp_request": ["n", "k", "blocks"],
+        "gp_response": ["status", "estimate_bytes", "peak_used_bytes"],
+    }
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gp.h"', "int main(void) {"]
+    for s, fields in checks.items():
+        lines.append(f'  printf("{s} %zu\\n", sizeof({s}));')
+        for f in fields:
+            lines.append(f'  printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    c = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for s, fields in checks.items():
+        t = getattr(gp, s)
+        assert int(c[s]) == ctypes.sizeof(t), s
+        for f in fields:
+            assert int(c[f"{s}.{f}"]) == getattr(t, f).offset, f"{s}.{f}"
